@@ -1,0 +1,259 @@
+"""Pins of the oracle's solvers (Sec. 5, Sec. 6.4).
+
+Each check uses a definition or an independent computation:
+* IC(0): (L L^T)_ij = A_ij on the pattern; IC(0) = dense Cholesky when the
+  pattern has no fill (one element: every function couples with every other);
+* level sets: longest paths of the factor's DAG computed with networkx;
+* PCG: dense direct solve; stopping rule at the first iterate meeting it;
+* MINRES: the defining optimality (eq. opt_condition, in the M^{-1} norm of
+  eq. linsys_precond) over the preconditioned Krylov space, computed densely;
+  a sparse direct solve of the bordered singular system;
+* adjoint: central finite differences of L = 1/2 ||u - u_t||^2.
+"""
+import networkx as nx
+import numpy as np
+import pytest
+import scipy.linalg as sl
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+
+def permuted_A(P):
+    perm, _, _ = P.ordering_arrays()
+    A = P.scipy("A").toarray()
+    return A[np.ix_(perm, perm)], perm
+
+
+@pytest.mark.parametrize("ordering", ["natural", "rcm", "multicolour"])
+@pytest.mark.parametrize("dim,N,p", [(2, 6, 3), (2, 4, 4), (3, 2, 3)])
+def test_ic0_defining_property(oracle_mod, ordering, dim, N, p):
+    P = oracle_mod.Problem(dim, N, p, ordering=ordering)
+    assert P.factor() < 0
+    Ah, perm = permuted_A(P)
+    L = P.scipy("L").toarray()
+    LLt = L @ L.T
+    pattern = np.zeros((P.n_u, P.n_u), dtype=bool)
+    ptr, col, _ = P.csr("L")
+    for i in range(P.n_u):
+        pattern[i, col[ptr[i]:ptr[i + 1]]] = True
+    # the pattern is exactly the lower triangle of the permuted pattern of A
+    ptrA, colA, _ = P.csr("A")
+    Apat = np.zeros((P.n_u, P.n_u), dtype=bool)
+    for i in range(P.n_u):
+        Apat[i, colA[ptrA[i]:ptrA[i + 1]]] = True
+    assert np.array_equal(pattern, np.tril(Apat[np.ix_(perm, perm)]))
+    err = np.abs(LLt - Ah)[pattern]
+    assert err.max() <= 1e-13 * np.abs(Ah).max()
+
+
+@pytest.mark.parametrize("ordering", ["natural", "rcm", "multicolour"])
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3)])
+def test_ic0_equals_cholesky_without_fill(oracle_mod, ordering, dim, p):
+    P = oracle_mod.Problem(dim, 1, p, ordering=ordering)
+    assert P.nnzA == P.n_u * P.n_u  # one element: dense pattern, no fill to drop
+    assert P.factor() < 0
+    Ah, _ = permuted_A(P)
+    L = P.scipy("L").toarray()
+    np.testing.assert_allclose(L, np.linalg.cholesky(Ah), atol=1e-13 * np.abs(Ah).max())
+
+
+def _levels_networkx(P):
+    ptr, col, _ = P.csr("L")
+    G = nx.DiGraph()
+    G.add_nodes_from(range(P.n_u))
+    for i in range(P.n_u):
+        for k in col[ptr[i]:ptr[i + 1]]:
+            if k < i:
+                G.add_edge(int(k), i)
+    lev = np.zeros(P.n_u, np.int32)
+    for g, nodes in enumerate(nx.topological_generations(G)):
+        lev[list(nodes)] = g
+    rlev = np.zeros(P.n_u, np.int32)
+    for g, nodes in enumerate(nx.topological_generations(G.reverse())):
+        rlev[list(nodes)] = g
+    return lev, rlev
+
+
+@pytest.mark.parametrize("ordering", ["natural", "rcm", "multicolour"])
+@pytest.mark.parametrize("dim,N,p", [(2, 7, 3), (2, 5, 4), (3, 3, 3), (3, 2, 2)])
+def test_level_sets_are_dag_longest_paths(oracle_mod, ordering, dim, N, p):
+    P = oracle_mod.Problem(dim, N, p, ordering=ordering)
+    _, lev, rlev = P.ordering_arrays()
+    lr, rr = _levels_networkx(P)
+    assert np.array_equal(lev, lr)
+    assert np.array_equal(rlev, rr)
+    if ordering == "multicolour":
+        ncol = dim * (p + 1) * p ** (dim - 1)
+        assert P.nlevels <= ncol and P.nrlevels <= ncol
+
+
+def test_orderings_are_permutations_and_rcm_reduces_bandwidth(oracle_mod):
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    for ordering in ("natural", "rcm", "multicolour"):
+        P = oracle_mod.Problem(2, 9, 3, ordering=ordering)
+        perm, _, _ = P.ordering_arrays()
+        assert np.array_equal(np.sort(perm), np.arange(P.n_u))
+
+    def bandwidth(A, perm):
+        B = A[perm][:, perm].tocoo()
+        return int(np.abs(B.row - B.col).max())
+
+    Pn = oracle_mod.Problem(2, 20, 3, ordering="natural")
+    Pr = oracle_mod.Problem(2, 20, 3, ordering="rcm")
+    A = Pn.scipy("A")
+    bw_nat = bandwidth(A, Pn.ordering_arrays()[0])
+    bw_rcm = bandwidth(A, Pr.ordering_arrays()[0])
+    bw_scipy = bandwidth(A, reverse_cuthill_mckee(A.tocsr(), symmetric_mode=True))
+    assert bw_rcm < bw_nat / 2
+    assert bw_rcm <= bw_scipy  # no worse than scipy's independent RCM
+
+
+@pytest.mark.parametrize("ordering", ["natural", "multicolour"])
+def test_pcg_matches_dense_solve_and_stops_at_first_iterate(oracle_mod, ordering):
+    P = oracle_mod.Problem(2, 5, 3, ordering=ordering)
+    assert P.factor() < 0
+    A = P.scipy("A").toarray()
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(P.n_u)
+    x, its = P.pcg(b, inner_tol=1e-13)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+    assert its <= P.n_u  # finite termination
+    # relaxed tolerance: the returned iterate meets it; one fewer would not
+    x, its = P.pcg(b, inner_tol=1e-2)
+    assert np.linalg.norm(b - A @ x) <= 1.0001e-2 * np.linalg.norm(b)
+    assert its >= 2
+    x1, its1 = P.pcg(b, inner_tol=1e-2, max_inner=its - 1)
+    assert its1 == its - 1
+    assert np.linalg.norm(b - A @ x1) > 1e-2 * np.linalg.norm(b)
+
+
+def test_pcg_with_exact_factor_takes_one_iteration(oracle_mod):
+    P = oracle_mod.Problem(2, 1, 3)
+    assert P.factor() < 0
+    b = np.random.default_rng(0).standard_normal(P.n_u)
+    x, its = P.pcg(b, inner_tol=1e-10)
+    assert its == 1
+    np.testing.assert_allclose(x, np.linalg.solve(P.scipy("A").toarray(), b), rtol=1e-9)
+
+
+def _stokes_dense(P):
+    A, B = P.scipy("A"), P.scipy("B")
+    return sp.bmat([[A, B.T], [B, None]]).toarray()
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 3, 2), (2, 2, 3), (3, 1, 2)])
+def test_minres_is_krylov_optimal_in_m_inverse_norm(oracle_mod, dim, N, p):
+    """With the inner solve converged (M_A = A), M = diag(A, Diag(Q_nu)) is a
+    fixed SPD matrix and x_j must minimise ||b - K x||_{M^{-1}} over
+    K_j(M^{-1} K, M^{-1} b); |eta_j| must equal that minimum."""
+    P = oracle_mod.Problem(dim, N, p)
+    assert P.factor() < 0
+    K = _stokes_dense(P)
+    n = P.n_u + P.n_p
+    A = P.scipy("A").toarray()
+    dq = P.scipy("Q").diagonal()
+    M = sl.block_diag(A, np.diag(dq / (2.0 * P.nu)))
+    R = np.linalg.cholesky(M)
+    rng = np.random.default_rng(11)
+    b = np.concatenate([rng.standard_normal(P.n_u), np.zeros(P.n_p)])
+    Minv = lambda v: np.linalg.solve(M, v)
+    gamma1 = np.sqrt(b @ Minv(b))
+    basis = []
+    v = Minv(b)
+    for j in range(1, 11):
+        # orthonormal basis of K_j(M^{-1}K, M^{-1}b)
+        w = v.copy()
+        for q in basis:
+            w -= (q @ w) * q
+        for q in basis:
+            w -= (q @ w) * q
+        if np.linalg.norm(w) < 1e-12 * np.linalg.norm(v):
+            break
+        basis.append(w / np.linalg.norm(w))
+        v = Minv(K @ basis[-1])
+        Vb = np.array(basis).T
+        Ls = np.linalg.solve(R, K @ Vb)
+        c, *_ = np.linalg.lstsq(Ls, np.linalg.solve(R, b), rcond=None)
+        best = np.linalg.norm(np.linalg.solve(R, b - K @ Vb @ c))
+        x, info = P.minres(b, tol=0.0, inner_tol=1e-14, max_outer=j)
+        assert info["outer"] == j
+        res = np.linalg.norm(np.linalg.solve(R, b - K @ x))
+        assert abs(res - best) <= 1e-8 * gamma1 + 1e-6 * best, (j, res, best)
+        assert abs(info["hist"][-1] * gamma1 - res) <= 1e-8 * gamma1 + 1e-6 * res
+        if best < 1e-10 * gamma1:
+            break
+
+
+def _direct_solve(P, rhs_u):
+    A, B = P.scipy("A"), P.scipy("B")
+    w = P.wmean()
+    K = sp.bmat([[A, B.T, None], [B, None, sp.csr_matrix(w.reshape(-1, 1))],
+                 [None, sp.csr_matrix(w.reshape(1, -1)), None]]).tocsc()
+    x = spl.spsolve(K, np.concatenate([rhs_u, np.zeros(P.n_p + 1)]))
+    return x[:P.n_u + P.n_p]
+
+
+@pytest.mark.parametrize("ordering", ["natural", "rcm", "multicolour"])
+def test_minres_matches_direct_solve_C1(oracle_mod, ordering):
+    """2D, 16x16 elements, k' = 2, manufactured forcing (Sec. 6.2)."""
+    P = oracle_mod.Problem(2, 16, 3, ordering=ordering)
+    assert P.factor() < 0
+    f = P.load_manufactured()
+    b = np.concatenate([f, np.zeros(P.n_p)])
+    xd = _direct_solve(P, f)
+    x, info = P.minres(b, tol=1e-13, inner_tol=1e-2)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+    x, info = P.minres(b, tol=1e-8, inner_tol=1e-2)
+    assert info["status"] == 0 and info["relres_est"] <= 1e-8
+    assert info["relres_true"] <= 1e-7
+    assert np.all(np.diff(info["hist"]) <= 1e-15)  # |eta| is non-increasing
+    assert abs(P.wmean() @ x[P.n_u:]) < 1e-12  # zero-mean pressure after the filter
+    # replay of the recorded inner counts reproduces the solve exactly
+    x2, info2 = P.minres(b, tol=1e-8, inner_tol=1e-2, forced=info["counts"])
+    assert np.array_equal(x, x2)
+    assert len(info["counts"]) == info["outer"] + 1
+
+
+def test_zero_rhs_and_breakdown_status(oracle_mod):
+    P = oracle_mod.Problem(2, 4, 3)
+    assert P.factor() < 0
+    x, info = P.minres(np.zeros(P.n_u + P.n_p))
+    assert info["status"] == 0 and info["outer"] == 0 and not x.any()
+    # a negative Nitsche constant makes A_h indefinite: IC(0) must report it
+    Pb = oracle_mod.Problem(2, 4, 3, cpen=-40.0)
+    assert Pb.factor() >= 0
+    assert not Pb.factored
+
+
+def test_adjoint_gradients_match_central_differences(oracle_mod):
+    """L(f, nu) = 1/2 ||u - u_t||^2 with K(nu) [u; p] = [f; 0].
+    dL/df = lambda_u and dL/dnu = -lambda_u^T A_0 u, where K lambda = [u - u_t; 0]
+    (K symmetric) and A_h = nu A_0 (linear in nu)."""
+    dim, N, p, nu = 2, 4, 3, 0.8
+    rng = np.random.default_rng(5)
+    kappa = rng.integers(1, 9, size=(16, dim)).astype(np.int32)
+    amp = rng.standard_normal((16, dim))
+    P = oracle_mod.Problem(dim, N, p, nu=nu)
+    assert P.factor() < 0
+    f = P.load_fourier(kappa, amp)
+    x, _ = P.minres(np.concatenate([f, np.zeros(P.n_p)]), tol=1e-13, inner_tol=1e-3)
+    u = x[:P.n_u]
+    ut = rng.standard_normal(P.n_u) * np.sqrt(np.mean(u ** 2))
+    lam, _ = P.minres(np.concatenate([u - ut, np.zeros(P.n_p)]), tol=1e-13, inner_tol=1e-3)
+    g_nu = P.dnu(lam[:P.n_u], u)
+
+    def loss(nu_, f_):
+        Q = oracle_mod.Problem(dim, N, p, nu=nu_)
+        uu = _direct_solve(Q, f_)[:Q.n_u]
+        return 0.5 * np.sum((uu - ut) ** 2)
+
+    h = 1e-6
+    fd = (loss(nu + h, f) - loss(nu - h, f)) / (2 * h)
+    assert abs(fd - g_nu) <= 1e-6 * abs(fd)
+    d = rng.standard_normal(P.n_u)
+    d /= np.linalg.norm(d)
+    eps = 1e-3  # L is quadratic in f: the central difference is exact
+    fd_f = (loss(nu, f + eps * d) - loss(nu, f - eps * d)) / (2 * eps)
+    assert abs(fd_f - lam[:P.n_u] @ d) <= 1e-7 * abs(fd_f)
