@@ -1,0 +1,197 @@
+/* gbstokes.h -- C ABI of the GB300 (sm_103a) Stokes solver library.
+ *
+ * Method (Cortes & Coutinho, arXiv:1309.5048): divergence-conforming
+ * (Raviart-Thomas type) B-spline discretisation of Stokes flow on the unit
+ * square or cube with Nitsche no-slip terms (Sec. 3.2, Sec. 4), solved by
+ * preconditioned MINRES (Sec. 5) with the block-diagonal preconditioner
+ * diag(M_A, M_Q) of Sec. 5.1: M_A^{-1} is a relaxed inner conjugate-gradient
+ * solve on A_h preconditioned by incomplete Cholesky IC(0) (Sec. 6.4), and
+ * M_Q = Diag(Q_nu), Q_nu = Q / (2 nu) (Sec. 5.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status:   every function returns GB_OK (0) or a GB_ERR_* code and never
+ *           throws; gb_last_error() gives a one-line message for the calling
+ *           thread.
+ * Memory:   arguments named *_dev are device pointers owned by the caller
+ *           (e.g. torch tensors); the library borrows them for the duration
+ *           of the call only.  *_host arguments are host memory.  The context
+ *           owns everything else (patterns, values, factors, workspaces).
+ * Streams:  all device work is ordered on the stream given to
+ *           gb_setup_pattern; calls that return host results synchronise it.
+ * Numbering: velocity DOFs are numbered component-major, then
+ *           lexicographically over the 1D function indices with the last
+ *           direction fastest; component c has degree p in direction c and
+ *           p-1 in the others, without its first and last function in
+ *           direction c (no-penetration space V_{0,h}, Sec. 3.2).  Pressure
+ *           DOFs (degree p-1, full space Q_h) are lexicographic the same way.
+ *           A solution or right-hand side vector is [u (n_u); p (n_p)].
+ * Batches:  k right-hand sides are stored RHS-major, [k][n] contiguous
+ *           (a row-major torch tensor of shape (k, n)); 1 <= k <= 32.
+ * Index width: matrices are stored with 32-bit column indices and row
+ *           pointers; problems with more than 2^31 - 1 nonzeros in one
+ *           matrix are rejected with GB_ERR_INVALID_ARG.
+ * Threading: a context may be used by one host thread at a time.
+ */
+#ifndef GBSTOKES_H
+#define GBSTOKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK 0
+#define GB_ERR_INVALID_ARG 1    /* bad size, pointer, option or call order */
+#define GB_ERR_CUDA 2           /* a CUDA runtime call failed */
+#define GB_ERR_OOM 3            /* device or host allocation failed */
+#define GB_ERR_IC0_BREAKDOWN 4  /* IC(0) met a non-positive pivot */
+#define GB_ERR_NOT_CONVERGED 5  /* iteration cap reached; outputs written */
+#define GB_ERR_NONFINITE 6      /* NaN/Inf met in the right-hand side or iterates */
+#define GB_ERR_DEVICE_TIMEOUT 7 /* a bounded device wait gave up */
+
+/* Orderings of A_h applied before IC(0).  The paper reorders A by reverse
+ * Cuthill-McKee (Sec. 6.4); natural and multicolour orderings are offered
+ * because the depth of the factor's DAG bounds the parallelism of the
+ * triangular solves. */
+#define GB_ORDER_NATURAL 0
+#define GB_ORDER_RCM 1
+#define GB_ORDER_MULTICOLOUR 2
+
+/* Precision of the inner preconditioner.  FP64 everywhere, or the inner
+ * IC(0)-CG in FP32 (FP32 copies of A_h and of the FP64 IC(0) factor, FP32
+ * vectors, FP64 across-thread reductions) with the outer MINRES recurrence,
+ * residual norms and the factorisation in FP64. */
+#define GB_PREC_FP64 0
+#define GB_PREC_MIXED 1
+
+typedef struct gb_ctx gb_ctx;
+
+typedef struct {
+  int dim;      /* 2 or 3 */
+  int N;        /* elements per direction, >= 1 */
+  int p;        /* velocity degree (pressure degree k' = p - 1), 2 <= p <= 6 */
+  int ordering; /* GB_ORDER_* */
+} gb_problem;
+
+typedef struct {
+  double tol;       /* outer stop: |eta_j| / gamma_1 <= tol (M^{-1}-norm residual
+                       ratio of eq. minimax_precond) */
+  double inner_tol; /* inner CG stop: ||r||_2 <= inner_tol ||b||_2 from x_0 = 0 */
+  int precision;    /* GB_PREC_* */
+  int max_outer;    /* MINRES iteration cap (>= 1) */
+  int max_inner;    /* inner CG iteration cap per application (>= 1) */
+  int use_graph;    /* 1: run the solve as one captured CUDA graph with device-
+                       side loop control; 0: host-driven loop */
+  const int32_t* forced_inner_host; /* optional (k == 1 only): replay mode.  The
+                       i-th preconditioner application runs exactly
+                       forced_inner_host[i] inner iterations, ignoring
+                       inner_tol.  NULL for normal operation. */
+  int64_t nforced;  /* length of forced_inner_host */
+} gb_solve_opts;
+
+typedef struct {
+  int outer_its;       /* MINRES iterations */
+  int precond_apps;    /* preconditioner applications (outer_its + 1) */
+  int64_t inner_its_total; /* inner CG iterations over all applications */
+  int inner_its_max;   /* largest inner count of one application */
+  double relres_est;   /* |eta| / gamma_1 at exit */
+  double relres_true;  /* ||b - K x||_2 / ||b||_2 recomputed at exit */
+  int status;          /* GB_OK, GB_ERR_NOT_CONVERGED or GB_ERR_NONFINITE */
+} gb_info;
+
+/* ---------------------------------------------------------------- setup --
+ * Builds the spaces (Sec. 3.2), the sparsity patterns of A_h, B, B^T (support
+ * overlap of the tensor-product B-splines), the ordering, the IC(0) pattern
+ * (lower triangle of the permuted A_h) with its level sets, and uploads them.
+ * `stream` is a cudaStream_t (NULL: legacy default stream).  On success *out
+ * receives a new context; release it with gb_destroy.  Host work: O(nnz). */
+int gb_setup_pattern(const gb_problem* prob, void* stream, gb_ctx** out);
+
+/* out[0..9] = n_u, n_p, nnz(A_h), nnz(B), nnz(L) (IC(0) factor incl. diagonal),
+ * number of forward levels, number of backward levels, nnz(Q) (structural),
+ * bytes of device memory held by the context, number of colours used by the
+ * ordering (0 unless multicolour). */
+int gb_sizes(const gb_ctx* ctx, int64_t* out_host);
+
+/* Assembles A_h = a - eta_h, B and Diag(Q) (Sec. 4: [A_h]_ij = a_h(Phi_j,Phi_i),
+ * [B]_kj = -(div Phi_j, phi_k), [Q]_kl = (phi_l, phi_k)) and w_k = (phi_k, 1)
+ * on the device.  nu > 0 is the viscosity; cpen is the Nitsche constant C_pen
+ * (<= 0 selects 5 (k' + 1), Sec. 6.2); h_F = 1/N.  Invalidates the factor. */
+int gb_assemble(gb_ctx* ctx, double nu, double cpen);
+
+/* Load vector f_i = (f, Phi_i) for the forcing
+ *   f_d(x) = sum_{m<nmodes} amp[m][d] prod_k sin(pi kappa[m][k] x_k)
+ * (kappa_host: int32 [nmodes][dim], amp_host: double [nmodes][dim]),
+ * integrated with p+3 Gauss points per direction and element.  f_dev: n_u
+ * doubles, natural numbering. */
+int gb_load_fourier(gb_ctx* ctx, int nmodes, const int32_t* kappa_host,
+                    const double* amp_host, double* f_dev);
+
+/* Load vector of the manufactured solution of Sec. 6.2 (2D only, the sign of
+ * u_2 taken so that div u = 0), f = -div(2 nu grad^s u) + grad p
+ * (eq. manufactured_force), with the nu of the last gb_assemble. */
+int gb_load_manufactured(gb_ctx* ctx, double* f_dev);
+
+/* IC(0) of the permuted A_h (Sec. 6.4): L L^T = A on the pattern of L, no
+ * fill, FP64, level-scheduled on the device; also builds the FP32 copies used
+ * by GB_PREC_MIXED.  On GB_ERR_IC0_BREAKDOWN *breakdown_row_host (may be NULL)
+ * receives the first offending row in the ordering's numbering. */
+int gb_factor_ic0(gb_ctx* ctx, int64_t* breakdown_row_host);
+
+/* Preconditioned MINRES (Sec. 5) on K x = b, K = [A_h B^T; B 0], for k
+ * right-hand sides at once, from x_0 = 0.  rhs_dev: [k][n_u + n_p] doubles;
+ * the pressure part of each rhs must satisfy 1^T g_p = 0 (K is singular with
+ * kernel [0; 1]); the pressure of x is filtered to zero mean,
+ * p <- p - (w^T p / w^T 1) 1 (Sec. 6.4).  x_dev: [k][n_u + n_p].  info_host:
+ * k entries.  Returns GB_ERR_NOT_CONVERGED if a RHS hit max_outer (its x is
+ * still written), GB_ERR_NONFINITE if a NaN/Inf was met. */
+int gb_solve(gb_ctx* ctx, const double* rhs_dev, double* x_dev, int k,
+             const gb_solve_opts* opts, gb_info* info_host);
+
+/* Same as gb_solve with host buffers: rhs_host and x_host are [k][n] host
+ * arrays (pinned memory recommended); copies are stream-ordered and the call
+ * returns after the results are in x_host. */
+int gb_solve_host(gb_ctx* ctx, const double* rhs_host, double* x_host, int k,
+                  const gb_solve_opts* opts, gb_info* info_host);
+
+/* Adjoint solve for a loss L(u, p) of a solution of gb_solve: K is symmetric
+ * (Sec. 5), so lambda solves K lambda = [dL/du; P^T dL/dp] with the same
+ * preconditioned MINRES, where P is the zero-mean pressure filter.
+ * grad_dev, lam_dev: [k][n_u + n_p].  dL/df = lambda_u.  Same options/info. */
+int gb_solve_adjoint(gb_ctx* ctx, const double* grad_dev, double* lam_dev, int k,
+                     const gb_solve_opts* opts, gb_info* info_host);
+
+/* dL/dnu = -lambda_u^T A_0 u for each of k pairs, with A_0 = A_h / nu (A_h is
+ * linear in nu, Sec. 3.1 and eq. nitsche_lhs) and f independent of nu.
+ * lam_dev, x_dev: [k][n_u + n_p]; out_host: k doubles. */
+int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
+
+/* y = K x (which = 0), y_u = A_h x_u (which = 1), y_p = B x_u (which = 2),
+ * y_u = B^T x_p (which = 3), all in natural numbering, FP64, one vector.
+ * x_dev / y_dev sizes follow the operator. */
+int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
+
+/* Copies internal arrays to the host for inspection and parity tests.
+ *  what 0: A_h CSR in natural numbering: rowptr int64 [n_u+1], col int32,
+ *          val double (any of the three pointers may be NULL)
+ *  what 1: B CSR (natural), same layout ([n_p+1] rowptr)
+ *  what 2: IC(0) factor L in the ordering's numbering (lower, diagonal
+ *          last in each row), same layout
+ *  what 3: ordering: p0 = int32 perm[new] = old (n_u); p1 = int32 forward
+ *          level per row in the ordering's numbering; p2 = int32 backward
+ *          level
+ *  what 4: Diag(Q) (p2 double [n_p]) and w (p1 double [n_p]) */
+int gb_export(gb_ctx* ctx, int what, void* p0, void* p1, void* p2);
+
+/* Releases all device and host memory of the context (NULL is allowed). */
+void gb_destroy(gb_ctx* ctx);
+
+const char* gb_status_string(int status);
+const char* gb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBSTOKES_H */

@@ -1,0 +1,298 @@
+"""gbstokes: GB300 (sm_103a) solver for the divergence-conforming B-spline
+Stokes system of Cortes & Coutinho (arXiv:1309.5048).
+
+This module is a thin ctypes binding of the C ABI in ``include/gbstokes.h``:
+it marshals arguments only (torch tensors provide device memory and the CUDA
+stream); every step of the method runs in the library's CUDA kernels.  There
+is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+ORDERINGS = {"natural": 0, "rcm": 1, "multicolour": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "IC(0) breakdown",
+          5: "not converged", 6: "non-finite value", 7: "device wait timed out"}
+GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_IC0_BREAKDOWN = 0, 5, 4
+
+
+class GbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gbstokes: %s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class gb_problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("p", C.c_int), ("ordering", C.c_int)]
+
+
+class gb_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("precision", C.c_int),
+                ("max_outer", C.c_int), ("max_inner", C.c_int), ("use_graph", C.c_int),
+                ("forced_inner_host", C.c_void_p), ("nforced", C.c_int64)]
+
+
+class gb_info(C.Structure):
+    _fields_ = [("outer_its", C.c_int), ("precond_apps", C.c_int), ("inner_its_total", C.c_int64),
+                ("inner_its_max", C.c_int), ("relres_est", C.c_double), ("relres_true", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
+            "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
+            "gb_export", "gb_destroy", "gb_status_string", "gb_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("gbstokes library missing at %s; run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        for name in EXPORTED:
+            getattr(L, name)  # every declared symbol must be exported
+        L.gb_setup_pattern.argtypes = [C.POINTER(gb_problem), vp, C.POINTER(vp)]
+        L.gb_sizes.argtypes = [vp, vp]
+        L.gb_assemble.argtypes = [vp, dbl, dbl]
+        L.gb_load_fourier.argtypes = [vp, i32, vp, vp, vp]
+        L.gb_load_manufactured.argtypes = [vp, vp]
+        L.gb_factor_ic0.argtypes = [vp, C.POINTER(i64)]
+        L.gb_solve.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
+        L.gb_solve_host.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
+        L.gb_solve_adjoint.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
+        L.gb_dnu.argtypes = [vp, vp, vp, i32, vp]
+        L.gb_apply.argtypes = [vp, i32, vp, vp]
+        L.gb_export.argtypes = [vp, i32, vp, vp, vp]
+        L.gb_destroy.argtypes = [vp]
+        L.gb_destroy.restype = None
+        L.gb_status_string.restype = C.c_char_p
+        L.gb_status_string.argtypes = [i32]
+        L.gb_last_error.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc, allow=()):
+    if rc != GB_OK and rc not in allow:
+        raise GbError(rc, load_library().gb_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Stokes:
+    """A discrete Stokes problem on the GPU (one context of the C library).
+
+    dim 2 or 3, N elements per direction, velocity degree p (pressure degree
+    p-1), ordering of A_h before IC(0): 'natural', 'rcm' or 'multicolour'.
+    All device work runs on the torch stream current at construction.
+    """
+
+    def __init__(self, dim, N, p, ordering="natural", device=None):
+        import torch
+        self.torch = torch
+        L = load_library()
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+        prob = gb_problem(dim, N, p, ORDERINGS[ordering])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.gb_setup_pattern(C.byref(prob), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.dim, self.N, self.p, self.ordering = dim, N, p, ordering
+        s = np.zeros(10, np.int64)
+        L.gb_sizes(h, s.ctypes.data_as(C.c_void_p))
+        (self.n_u, self.n_p, self.nnzA, self.nnzB, self.nnzL, self.nlevels, self.nrlevels,
+         self.nnzQ, self.device_bytes, self.ncolours) = (int(v) for v in s)
+        self.n = self.n_u + self.n_p
+        self.nu = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().gb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, x, shape=None):
+        t = self.torch.as_tensor(x, dtype=self.torch.float64, device=self.device).contiguous()
+        if shape is not None:
+            t = t.reshape(shape)
+        return t
+
+    # ------------------------------------------------------------ set-up
+    def assemble(self, nu=1.0, cpen=None):
+        _check(load_library().gb_assemble(self._h, float(nu), -1.0 if cpen is None else float(cpen)))
+        self.nu = float(nu)
+
+    def load_fourier(self, kappa, amp):
+        kappa = np.ascontiguousarray(kappa, dtype=np.int32)
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        f = self.torch.empty(self.n_u, dtype=self.torch.float64, device=self.device)
+        _check(load_library().gb_load_fourier(self._h, kappa.shape[0], kappa.ctypes.data_as(C.c_void_p),
+                                              amp.ctypes.data_as(C.c_void_p), _ptr(f)))
+        return f
+
+    def load_manufactured(self):
+        f = self.torch.empty(self.n_u, dtype=self.torch.float64, device=self.device)
+        _check(load_library().gb_load_manufactured(self._h, _ptr(f)))
+        return f
+
+    def factor_ic0(self):
+        """IC(0) of the reordered A_h; returns -1, or raises GbError with the
+        breakdown row in ``.row``."""
+        row = C.c_int64(-1)
+        rc = load_library().gb_factor_ic0(self._h, C.byref(row))
+        if rc == GB_ERR_IC0_BREAKDOWN:
+            e = GbError(rc, "non-positive pivot at row %d" % row.value)
+            e.row = row.value
+            raise e
+        _check(rc)
+        return -1
+
+    # ------------------------------------------------------------ solves
+    @staticmethod
+    def options(tol=1e-8, inner_tol=1e-2, precision="fp64", max_outer=5000, max_inner=1000,
+                use_graph=True, forced=None):
+        o = gb_solve_opts(tol, inner_tol, PRECISIONS[precision], max_outer, max_inner, int(use_graph), None, 0)
+        keep = None
+        if forced is not None:
+            keep = np.ascontiguousarray(forced, dtype=np.int32)
+            o.forced_inner_host = keep.ctypes.data_as(C.c_void_p)
+            o.nforced = keep.size
+        return o, keep
+
+    def _solve(self, fn, rhs, out=None, allow_not_converged=True, **kw):
+        rhs = self._dev(rhs)
+        single = rhs.dim() == 1
+        rhs2 = rhs.reshape(-1, self.n)
+        k = rhs2.shape[0]
+        x = out if out is not None else self.torch.empty_like(rhs2)
+        o, keep = self.options(**kw)
+        infos = (gb_info * k)()
+        rc = fn(self._h, _ptr(rhs2), _ptr(x), k, C.byref(o), infos)
+        del keep
+        _check(rc, allow=(GB_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        info = [infos[i].as_dict() for i in range(k)]
+        return (x[0] if single else x), (info[0] if single else info)
+
+    def solve(self, rhs, out=None, **kw):
+        """Preconditioned MINRES from x0 = 0 for rhs of shape (n,) or (k, n),
+        k <= 32.  Options: tol, inner_tol, precision ('fp64'|'mixed'),
+        max_outer, max_inner, use_graph, forced (replay inner counts)."""
+        return self._solve(load_library().gb_solve, rhs, out, **kw)
+
+    def solve_adjoint(self, grad, out=None, **kw):
+        return self._solve(load_library().gb_solve_adjoint, grad, out, **kw)
+
+    def solve_host(self, rhs_host, out_host=None, **kw):
+        """gb_solve_host: host (pinned) buffers in and out."""
+        import torch
+        rhs_host = torch.as_tensor(rhs_host, dtype=torch.float64).contiguous()
+        rhs2 = rhs_host.reshape(-1, self.n)
+        k = rhs2.shape[0]
+        x = out_host if out_host is not None else torch.empty_like(rhs2, pin_memory=True)
+        o, keep = self.options(**kw)
+        infos = (gb_info * k)()
+        rc = load_library().gb_solve_host(self._h, C.c_void_p(rhs2.data_ptr()), C.c_void_p(x.data_ptr()), k,
+                                          C.byref(o), infos)
+        _check(rc, allow=(GB_ERR_NOT_CONVERGED,))
+        return x, [infos[i].as_dict() for i in range(k)]
+
+    def dnu(self, lam, x):
+        lam = self._dev(lam).reshape(-1, self.n)
+        x = self._dev(x).reshape(-1, self.n)
+        k = lam.shape[0]
+        out = np.zeros(k)
+        _check(load_library().gb_dnu(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def apply(self, which, x):
+        """which: 'K' (Stokes operator), 'A', 'B', 'Bt' -- natural numbering."""
+        w = {"K": 0, "A": 1, "B": 2, "Bt": 3}[which]
+        x = self._dev(x)
+        nout = {"K": self.n, "A": self.n_u, "B": self.n_p, "Bt": self.n_u}[which]
+        y = self.torch.empty(nout, dtype=self.torch.float64, device=self.device)
+        _check(load_library().gb_apply(self._h, w, _ptr(x), _ptr(y)))
+        return y
+
+    # ------------------------------------------------------------ export
+    def csr(self, which):
+        """('A'|'B'|'L') -> (indptr int64, indices int32, data float64) on the host."""
+        L = load_library()
+        w = {"A": 0, "B": 1, "L": 2}[which]
+        nrows = {"A": self.n_u, "B": self.n_p, "L": self.n_u}[which]
+        nnz = {"A": self.nnzA, "B": self.nnzB, "L": self.nnzL}[which]
+        ptr = np.zeros(nrows + 1, np.int64)
+        col = np.zeros(nnz, np.int32)
+        val = np.zeros(nnz, np.float64)
+        _check(L.gb_export(self._h, w, ptr.ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+                           val.ctypes.data_as(C.c_void_p)))
+        return ptr, col, val
+
+    def ordering_arrays(self):
+        perm = np.zeros(self.n_u, np.int32)
+        lev = np.zeros(self.n_u, np.int32)
+        rlev = np.zeros(self.n_u, np.int32)
+        _check(load_library().gb_export(self._h, 3, perm.ctypes.data_as(C.c_void_p),
+                                        lev.ctypes.data_as(C.c_void_p), rlev.ctypes.data_as(C.c_void_p)))
+        return perm, lev, rlev
+
+    def pressure_arrays(self):
+        w = np.zeros(self.n_p)
+        q = np.zeros(self.n_p)
+        _check(load_library().gb_export(self._h, 4, None, w.ctypes.data_as(C.c_void_p),
+                                        q.ctypes.data_as(C.c_void_p)))
+        return w, q
+
+
+# Function-style names matching the C ABI.
+def setup_pattern(dim, N, p, ordering="natural", device=None) -> Stokes:
+    return Stokes(dim, N, p, ordering, device)
+
+
+def assemble(s: Stokes, nu=1.0, cpen=None):
+    return s.assemble(nu, cpen)
+
+
+def factor_ic0(s: Stokes):
+    return s.factor_ic0()
+
+
+def solve(s: Stokes, rhs, **kw):
+    return s.solve(rhs, **kw)
+
+
+def solve_adjoint(s: Stokes, grad, **kw):
+    return s.solve_adjoint(grad, **kw)

@@ -1,0 +1,115 @@
+// factor.cu -- IC(0) factorisation of the (reordered) A_h on the device.
+//
+// Sec. 6.4: incomplete Cholesky with zero fill, L L^T = A on every position
+// of the lower pattern.  Row i is computed from earlier rows k:
+//   L_ik = (A_ik - sum_{j < k, j in pat(i) and pat(k)} L_ij L_kj) / L_kk,
+//   L_ii = sqrt(A_ii - sum_{k < i} L_ik^2).
+// In the internal numbering the rows of one DAG level are contiguous and
+// independent, so each level is one launch with one warp per row.  Within a
+// row the columns are taken in increasing order (each L_ik needs the L_ij,
+// j < k, of the same row); the lanes share the sparse dot product with row k.
+#include <cmath>
+
+#include "gbs_device.cuh"
+#include "gbs_internal.h"
+
+namespace gbs {
+
+namespace {
+
+// A row of L (strict lower part) is the prefix of the same row of A.
+__global__ void k_ic0_level(int r0, int r1, const int32_t* __restrict__ A_ptr,
+                            const int32_t* __restrict__ A_diag, const double* __restrict__ A_val,
+                            const int32_t* __restrict__ L_ptr, const int32_t* __restrict__ L_col,
+                            const int32_t* __restrict__ pos, double* L_val, double* L_diag,
+                            double* L_inv, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int r = r0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (r >= r1) return;
+  const int lb = L_ptr[r], le = L_ptr[r + 1];
+  const int ab = A_ptr[r];
+  double diag_acc = 0.0;
+  for (int t = lb; t < le; ++t) {
+    const int k = L_col[t];
+    // sum over j < k in row k that also occur in row r (positions lb .. t-1)
+    double part = 0.0;
+    const int kb = L_ptr[k], ke = L_ptr[k + 1];
+    for (int u = kb + lane; u < ke; u += 32) {
+      const int j = L_col[u];
+      int lo = lb, hi = t;  // binary search for column j among row r's first entries
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (L_col[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      // entries of row r were written by lane 0 during this launch: read via L2
+      if (lo < t && L_col[lo] == j) part += __ldcg(&L_val[lo]) * L_val[u];
+    }
+    part = warp_sum(part);
+    const double lik = (A_val[ab + (t - lb)] - part) / L_diag[k];
+    if (lane == 0) L_val[t] = lik;
+    diag_acc += lik * lik;  // identical in every lane
+    __syncwarp();
+  }
+  if (lane == 0) {
+    const double piv = A_val[A_diag[r]] - diag_acc;
+    if (!(piv > 0.0)) {
+      atomicMin(&status[0], pos[r]);  // first bad row in ordering numbering
+      L_diag[r] = 1.0;
+      L_inv[r] = 0.0;
+    } else {
+      const double d = sqrt(piv);
+      L_diag[r] = d;
+      L_inv[r] = 1.0 / d;
+    }
+  }
+}
+
+__global__ void k_factor_finish(int n, int nnzL, int nnzU, const double* __restrict__ L_val,
+                                const double* __restrict__ L_inv, const int32_t* __restrict__ U_map,
+                                double* __restrict__ U_val, float* __restrict__ L_val32,
+                                float* __restrict__ U_val32, float* __restrict__ L_inv32) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nnzU; t += stride) {
+    const double v = L_val[U_map[t]];
+    U_val[t] = v;
+    U_val32[t] = (float)v;
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nnzL; t += stride) L_val32[t] = (float)L_val[t];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) L_inv32[t] = (float)L_inv[t];
+}
+
+}  // namespace
+
+int64_t factor_ic0(Ctx& c) {
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble before factor_ic0");
+  const int n = (int)c.n_u;
+  const int init = INT32_MAX;
+  GBS_CUDA(cudaMemcpyAsync(c.status_d.p, &init, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  for (int l = 0; l < c.nlev; ++l) {
+    const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
+    const int warps = r1 - r0;
+    const int block = 256;
+    const int grid = (warps * 32 + block - 1) / block;
+    k_ic0_level<<<grid, block, 0, c.stream>>>(r0, r1, c.A_ptr.p, c.A_diag.p, c.A_val.p, c.L_ptr.p,
+                                              c.L_col.p, c.pos_d.p, c.L_val.p, c.L_diag.p, c.L_inv.p,
+                                              c.status_d.p);
+  }
+  GBS_CUDA(cudaGetLastError());
+  const int nnzL = (int)(c.nnzL - c.n_u), nnzU = nnzL;
+  k_factor_finish<<<152 * 8, 256, 0, c.stream>>>(n, nnzL, nnzU, c.L_val.p, c.L_inv.p, c.U_map.p,
+                                                 c.U_val.p, c.L_val32.p, c.U_val32.p, c.L_inv32.p);
+  GBS_CUDA(cudaGetLastError());
+  int bad = 0;
+  GBS_CUDA(cudaMemcpyAsync(&bad, c.status_d.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  c.ws.graph_valid = false;
+  if (bad != INT32_MAX) {
+    c.factored = false;
+    return bad;  // row in the ordering's numbering
+  }
+  c.factored = true;
+  return -1;
+}
+
+}  // namespace gbs

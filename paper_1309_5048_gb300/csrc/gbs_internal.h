@@ -1,0 +1,182 @@
+// gbs_internal.h -- private declarations of the gbstokes library.
+//
+// Device data layout
+// ------------------
+// Velocity unknowns are stored in an *internal* numbering: the rows of the
+// chosen ordering (natural / RCM / multicolour) sorted by their level in the
+// IC(0) factor's DAG (stable, so ties keep the ordering's order).  Sorting by
+// level is a topological order of that DAG, so the IC(0) factor is unchanged
+// (every coupled pair keeps its relative order) while each level becomes a
+// contiguous row range.  Pressure unknowns keep the natural numbering.
+//
+//   A_h      CSR (int32 ptr/col, FP64 val, FP32 copy), rows/cols internal,
+//            sorted columns; the strictly-lower part of row i is a prefix.
+//   L        strict lower part of the IC(0) factor, CSR (internal numbering),
+//            plus 1/L_ii; U = L^T strict upper part in CSR (row form of the
+//            backward solve), values gathered from L through U_map.
+//   B        CSR, rows = pressure (natural), cols = velocity (internal).
+//   Bt       CSR of B^T, rows = velocity (internal), values from B via Bt_map.
+//   vectors  [n][K] interleaved: entry (row, rhs) at row*K + rhs, K the padded
+//            batch width (1, 8 or 32).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gbstokes.h"
+
+namespace gbs {
+
+// Error raised inside the library; converted to a status at the C boundary.
+struct Error {
+  int status;
+  std::string msg;
+};
+[[noreturn]] void fail(int status, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define GBS_CUDA(call) ::gbs::cuda_check((call), #call)
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { free_(); }
+  void alloc(size_t count);
+  void free_();
+  void upload(const T* host, size_t count, cudaStream_t s);
+  void zero(cudaStream_t s);
+};
+
+// Reduction buffer: per-block partials and a completion counter; the last
+// block to finish reduces the partials in a fixed order (deterministic).
+struct RedBuf {
+  double* partial = nullptr;  // [maxblocks][K][nsums]
+  unsigned* counter = nullptr;
+};
+
+// Per-RHS scalar state of the solver, structure of arrays [field][K].
+enum ScalarField {
+  // MINRES
+  S_GAMMA, S_GAMMA_PREV, S_GAMMA1, S_ETA, S_C, S_C_PREV, S_S, S_S_PREV, S_DELTA,
+  S_XCOEF, S_A1, S_A2, S_A3, S_BNORM, S_RELRES, S_OUTER_ACTIVE, S_OUTER_ITS, S_STATUS,
+  // inner CG
+  S_RHO, S_ALPHA, S_CG_BNORM, S_RNORM, S_CG_ITS, S_CG_ACTIVE, S_CG_TARGET,
+  // statistics
+  S_INNER_TOTAL, S_INNER_MAX, S_APPS, S_TRUE_RES, S_NONFINITE, S_PMEAN,
+  S_NFIELDS
+};
+
+struct Workspace {
+  int K = 0;          // padded batch width
+  int k = 0;          // live right-hand sides
+  int precision = -1;
+  size_t n = 0;       // n_u + n_p
+  // MINRES (FP64): x, three Lanczos vectors, two z buffers, three w buffers, q
+  double* x = nullptr;
+  double* V[3] = {nullptr, nullptr, nullptr};
+  double* Z[2] = {nullptr, nullptr};
+  double* W[3] = {nullptr, nullptr, nullptr};
+  double* q = nullptr;
+  double* b = nullptr;  // right-hand side, internal layout
+  // inner CG, element type T (double or float) stored as raw bytes
+  void* cg_x = nullptr;
+  void* cg_r = nullptr;
+  void* cg_z = nullptr;
+  void* cg_y = nullptr;
+  void* cg_p = nullptr;
+  void* cg_q = nullptr;
+  void* cg_b = nullptr;
+  double* S = nullptr;          // scalars [S_NFIELDS][K]
+  double* S_host = nullptr;     // pinned mirror
+  int* flag = nullptr;          // device: [0] any outer active, [1] any inner active
+  int* flag_host = nullptr;     // pinned
+  int32_t* forced = nullptr;    // device replay counts
+  int64_t nforced = 0;
+  size_t forced_cap = 0;
+  double* partial = nullptr;    // reduction partials [blocks][K][<=4]
+  unsigned* counter = nullptr;  // completion counter of the reduction kernels
+  double* aux = nullptr;        // small scratch (adjoint coefficients, dnu partials)
+  double* rhs_tmp = nullptr;    // adjoint right-hand side [k][n]
+  double* host_in = nullptr;    // device staging for gb_solve_host
+  double* host_out = nullptr;
+  // CUDA graph of the whole solve (device-side loop control)
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
+  bool graph_valid = false;
+};
+
+struct Ctx {
+  gb_problem prob{};
+  // All device work runs on `stream`, a non-blocking stream owned by the
+  // context (graphs cannot be captured on the legacy default stream); every
+  // API call orders it after the caller's stream on entry and the caller's
+  // stream after it on exit, with events.
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int dim = 2, N = 1, p = 2;
+  int64_t n_u = 0, n_p = 0, nnzA = 0, nnzB = 0, nnzL = 0, nnzQ = 0;
+  int nlev = 0, nrlev = 0, ncolours = 0;
+  // host copies
+  std::vector<int32_t> order;    // internal -> natural velocity index
+  std::vector<int32_t> perm;     // ordering position -> natural
+  std::vector<int32_t> int_to_pos;  // internal -> ordering position
+  std::vector<int32_t> level, rlevel;  // by ordering position
+  std::vector<int32_t> lev_ptr;  // forward level l = internal rows [lev_ptr[l], lev_ptr[l+1])
+  std::vector<int32_t> hA_ptr, hA_col;  // internal CSR pattern of A
+  std::vector<int32_t> hB_ptr, hB_col;  // B pattern (cols internal)
+  // device arrays
+  DevBuf<int32_t> order_d, iorder_d, pos_d;  // pos_d: internal -> ordering position
+  DevBuf<int32_t> A_ptr, A_col, A_diag;  // A_diag[i]: position of the diagonal
+  DevBuf<double> A_val;
+  DevBuf<float> A_val32;
+  DevBuf<int32_t> L_ptr, L_col;
+  DevBuf<double> L_val, L_diag, L_inv;
+  DevBuf<float> L_val32, L_inv32;
+  DevBuf<int32_t> U_ptr, U_col, U_map;
+  DevBuf<double> U_val;
+  DevBuf<float> U_val32;
+  DevBuf<int32_t> B_ptr, B_col, Bt_ptr, Bt_col, Bt_map;
+  DevBuf<double> B_val, Bt_val;
+  DevBuf<double> Qdiag, wmean;
+  DevBuf<double> tab1d;  // 1D integral tables (assembly)
+  DevBuf<int> status_d;  // device error flags
+  double nu = 1.0, cpen = 0.0;
+  bool assembled = false, factored = false;
+  Workspace ws;
+  size_t device_bytes = 0;
+};
+
+// setup.cpp
+void setup_pattern(Ctx& c, const gb_problem& prob);
+// assemble.cu
+void assemble(Ctx& c, double nu, double cpen);
+void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, double* f_dev);
+void load_manufactured(Ctx& c, double* f_dev);
+// factor.cu
+int64_t factor_ic0(Ctx& c);
+// solver.cu
+int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts& o,
+          gb_info* info, bool adjoint);
+int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_solve_opts& o,
+               gb_info* info);
+void apply_operator(Ctx& c, int which, const double* x, double* y);
+void dnu(Ctx& c, const double* lam, const double* x, int k, double* out);
+void release_workspace(Ctx& c);
+
+// Velocity DOF decoding shared by host setup code.
+struct Space {
+  int dim, N, p;
+  int64_t voff[4];
+  int deg(int c, int k) const { return k == c ? p : p - 1; }
+  int vlen(int c, int k) const { return k == c ? N + p - 2 : N + p - 1; }
+  int plen() const { return N + p - 1; }
+};
+
+}  // namespace gbs

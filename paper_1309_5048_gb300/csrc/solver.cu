@@ -1,0 +1,444 @@
+// solver.cu -- host driver of the preconditioned MINRES solve (Sec. 5).
+//
+// The kernel sequence of one solve (see solver_kernels.cuh) is
+//   gather, z_1 = M^{-1} b (Lanczos j=0, inner CG), gamma_1,
+//   repeat { K z_j, Lanczos, inner CG, Givens, w/x update } while any RHS live,
+//   true residual, zero-mean filter and scatter.
+// Loop control is on the device: the last block of the CG and MINRES step
+// kernels decides whether any RHS is still active.  Two drivers run the same
+// sequence: a host loop that reads that flag (one synchronisation per inner
+// iteration), and a CUDA graph whose loops are WHILE conditional nodes set by
+// those kernels (no host round trip during the solve).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "solver_kernels.cuh"
+
+namespace gbs {
+
+namespace {
+
+void* dmalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(GB_ERR_OOM, "cudaMalloc failed for workspace");
+  }
+  return p;
+}
+
+void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
+  Workspace& w = c.ws;
+  const size_t n = (size_t)(c.n_u + c.n_p);
+  if (!(w.K == K && w.precision == precision && w.n == n && w.x)) {
+    release_workspace(c);
+    w.K = K;
+    w.precision = precision;
+    w.n = n;
+    const size_t esz = precision == GB_PREC_MIXED ? 4 : 8;
+    const size_t vb = n * K * sizeof(double), cb = (size_t)c.n_u * K * esz;
+    w.x = (double*)dmalloc(vb);
+    for (int i = 0; i < 3; ++i) w.V[i] = (double*)dmalloc(vb);
+    for (int i = 0; i < 2; ++i) w.Z[i] = (double*)dmalloc(vb);
+    for (int i = 0; i < 3; ++i) w.W[i] = (double*)dmalloc(vb);
+    w.q = (double*)dmalloc(vb);
+    w.b = (double*)dmalloc(vb);
+    w.cg_x = dmalloc(cb);
+    w.cg_r = dmalloc(cb);
+    w.cg_z = dmalloc(cb);
+    w.cg_y = dmalloc(cb);
+    w.cg_p = dmalloc(cb);
+    w.cg_q = dmalloc(cb);
+    w.S = (double*)dmalloc(sizeof(double) * S_NFIELDS * K);
+    GBS_CUDA(cudaMallocHost((void**)&w.S_host, sizeof(double) * S_NFIELDS * K));
+    w.flag = (int*)dmalloc(sizeof(int) * 8);
+    GBS_CUDA(cudaMallocHost((void**)&w.flag_host, sizeof(int) * 8));
+    w.partial = (double*)dmalloc(sizeof(double) * kRB * 32 * 4);
+    w.counter = (unsigned*)dmalloc(64);
+    w.aux = (double*)dmalloc(sizeof(double) * kRB * 32);
+    GBS_CUDA(cudaMemsetAsync(w.counter, 0, 64, c.stream));
+    GBS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int) * 8, c.stream));
+    GBS_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * S_NFIELDS * K, c.stream));
+    w.graph_valid = false;
+  }
+  if (k_io > 0 && w.k < k_io) {
+    if (w.rhs_tmp) cudaFree(w.rhs_tmp);
+    if (w.host_in) cudaFree(w.host_in);
+    if (w.host_out) cudaFree(w.host_out);
+    w.rhs_tmp = (double*)dmalloc(sizeof(double) * n * k_io);
+    w.host_in = (double*)dmalloc(sizeof(double) * n * k_io);
+    w.host_out = (double*)dmalloc(sizeof(double) * n * k_io);
+    w.k = k_io;
+    w.graph_valid = false;
+  }
+}
+
+Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
+  Workspace& w = c.ws;
+  Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_u = (int)c.n_u;
+  a.n_p = (int)c.n_p;
+  a.k = k;
+  a.A_ptr = c.A_ptr.p;
+  a.A_col = c.A_col.p;
+  a.A_val = c.A_val.p;
+  a.A_val32 = c.A_val32.p;
+  a.L_ptr = c.L_ptr.p;
+  a.L_col = c.L_col.p;
+  a.L_val = c.L_val.p;
+  a.L_inv = c.L_inv.p;
+  a.L_val32 = c.L_val32.p;
+  a.L_inv32 = c.L_inv32.p;
+  a.U_ptr = c.U_ptr.p;
+  a.U_col = c.U_col.p;
+  a.U_val = c.U_val.p;
+  a.U_val32 = c.U_val32.p;
+  a.B_ptr = c.B_ptr.p;
+  a.B_col = c.B_col.p;
+  a.B_val = c.B_val.p;
+  a.Bt_ptr = c.Bt_ptr.p;
+  a.Bt_col = c.Bt_col.p;
+  a.Bt_val = c.Bt_val.p;
+  a.Qdiag = c.Qdiag.p;
+  a.wmean = c.wmean.p;
+  a.order = c.order_d.p;
+  a.nu = c.nu;
+  a.x = w.x;
+  a.V0 = w.V[0];
+  a.V1 = w.V[1];
+  a.V2 = w.V[2];
+  a.Z0 = w.Z[0];
+  a.Z1 = w.Z[1];
+  a.W0 = w.W[0];
+  a.W1 = w.W[1];
+  a.W2 = w.W[2];
+  a.q = w.q;
+  a.b = w.b;
+  a.cg_x = w.cg_x;
+  a.cg_r = w.cg_r;
+  a.cg_z = w.cg_z;
+  a.cg_y = w.cg_y;
+  a.cg_p = w.cg_p;
+  a.cg_q = w.cg_q;
+  a.S = w.S;
+  a.flag = w.flag;
+  a.jcur = w.flag + 2;
+  a.partial = w.partial;
+  a.counter = w.counter;
+  if (o) {
+    a.tol = o->tol;
+    a.inner_tol = o->inner_tol;
+    a.max_outer = o->max_outer;
+    a.max_inner = o->max_inner;
+    a.forced = o->forced_inner_host ? w.forced : nullptr;
+    a.nforced = o->forced_inner_host ? (int)o->nforced : 0;
+  }
+  return a;
+}
+
+int grid_cap(int64_t threads) {
+  int64_t g = (threads + kBlock - 1) / kBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, kRB));
+}
+
+template <int K, class T>
+struct Run {
+  Ctx& c;
+  Args a;
+  cudaStream_t s;
+  static constexpr int G = Map<K>::G;
+  Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {}
+  int64_t n() const { return c.n_u + c.n_p; }
+
+  void gather(const double* rhs) { k_gather<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a, rhs); }
+  void lanczos() { k_lanczos<K, T><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
+  void stokes() { k_stokes_apply<K><<<grid_cap(n() * G), kBlock, 0, s>>>(a); }
+  void gamma() { k_gamma<K, T><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
+  void update() { k_update<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
+  void trsv_fwd() {
+    for (int l = 0; l < c.nlev; ++l) {
+      const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
+      const int64_t th = (int64_t)(r1 - r0) * G;
+      k_trsv_level<K, T, true><<<(unsigned)((th + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r0, r1);
+    }
+  }
+  void trsv_bwd() {
+    for (int l = c.nlev - 1; l >= 0; --l) {
+      const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
+      const int64_t th = (int64_t)(r1 - r0) * G;
+      k_trsv_level<K, T, false><<<(unsigned)((th + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r0, r1);
+    }
+  }
+  void cg_prologue() {
+    trsv_fwd();
+    trsv_bwd();
+    k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 1);
+  }
+  void cg_head() {
+    k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
+    k_cg_axpy<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
+  }
+  void cg_tail() {
+    trsv_fwd();
+    trsv_bwd();
+    k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 0);
+    k_cg_pupdate<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
+  }
+  void finish(double* out) {
+    k_residual<K><<<grid_cap(n() * G), kBlock, 0, s>>>(a);
+    k_scatter<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a, out);
+  }
+
+  int read_flag(int i) {
+    GBS_CUDA(cudaMemcpyAsync(c.ws.flag_host, c.ws.flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    GBS_CUDA(cudaStreamSynchronize(s));
+    return c.ws.flag_host[i];
+  }
+  void cg_loop_host() {
+    for (;;) {
+      cg_head();
+      if (!read_flag(1)) break;
+      cg_tail();
+    }
+  }
+  void run_host(const double* rhs, double* out) {
+    a.use_handles = 0;
+    gather(rhs);
+    lanczos();
+    cg_prologue();
+    cg_loop_host();
+    gamma();
+    while (read_flag(0)) {
+      stokes();
+      lanczos();
+      cg_prologue();
+      cg_loop_host();
+      gamma();
+      update();
+    }
+    finish(out);
+    GBS_CUDA(cudaGetLastError());
+  }
+
+  // --- CUDA graph with device-side loop control
+  cudaGraph_t add_while(cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    GBS_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, &ed, &nd));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // aggregate init (no default ctor)
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    GBS_CUDA(cudaGraphAddNode(&node, cg, deps, ed, nd, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    GBS_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return body;
+  }
+  template <class F>
+  void capture_into(cudaGraph_t g, F fn) {
+    GBS_CUDA(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    fn();
+    cudaGraph_t out = nullptr;
+    GBS_CUDA(cudaStreamEndCapture(s, &out));
+  }
+  cudaGraphExec_t build_graph(const double* rhs, double* out) {
+    cudaGraph_t g;
+    GBS_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h_out, h_in0, h_in;
+    GBS_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 0, 0));
+    GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in0, g, 0, 0));
+    const Args base = a;
+    a.use_handles = 1;
+    a.h_outer = h_out;
+    a.h_inner = h_in0;
+    cudaGraph_t body0 = nullptr, bodyO = nullptr, bodyI = nullptr;
+    capture_into(g, [&] {
+      gather(rhs);
+      lanczos();
+      cg_prologue();
+      body0 = add_while(h_in0);
+      gamma();
+      bodyO = add_while(h_out);
+      finish(out);
+    });
+    capture_into(body0, [&] {
+      cg_head();
+      cg_tail();
+    });
+    GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in, bodyO, 0, 0));
+    a.h_inner = h_in;
+    capture_into(bodyO, [&] {
+      stokes();
+      lanczos();
+      cg_prologue();
+      bodyI = add_while(h_in);
+      gamma();
+      update();
+    });
+    capture_into(bodyI, [&] {
+      cg_head();
+      cg_tail();
+    });
+    a = base;
+    cudaGraphExec_t exec = nullptr;
+    GBS_CUDA(cudaGraphInstantiate(&exec, g, 0));
+    GBS_CUDA(cudaGraphDestroy(g));
+    return exec;
+  }
+};
+
+template <int K, class T>
+void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solve_opts& o) {
+  Args a = make_args(c, &o, k);
+  Run<K, T> run(c, a);
+  Workspace& w = c.ws;
+  if (!o.use_graph) {
+    run.run_host(rhs, out);
+    return;
+  }
+  std::vector<double> key = {(double)(uintptr_t)rhs, (double)(uintptr_t)out, (double)k, o.tol, o.inner_tol,
+                             (double)o.max_outer, (double)o.max_inner, (double)K, (double)o.precision,
+                             (double)a.nforced, c.nu};
+  if (!w.graph_valid || w.graph_key != key) {
+    if (w.graph) {
+      cudaGraphExecDestroy(w.graph);
+      w.graph = nullptr;
+    }
+    w.graph = run.build_graph(rhs, out);
+    w.graph_key = key;
+    w.graph_valid = true;
+  }
+  GBS_CUDA(cudaGraphLaunch(w.graph, c.stream));
+}
+
+int collect_info(Ctx& c, int k, gb_info* info) {
+  Workspace& w = c.ws;
+  const int K = w.K;
+  GBS_CUDA(cudaMemcpyAsync(w.S_host, w.S, sizeof(double) * S_NFIELDS * K, cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  int worst = GB_OK;
+  for (int t = 0; t < k; ++t) {
+    auto f = [&](int field) { return w.S_host[field * K + t]; };
+    gb_info& I = info[t];
+    I.outer_its = (int)f(S_OUTER_ITS);
+    I.precond_apps = (int)f(S_APPS);
+    I.inner_its_total = (int64_t)f(S_INNER_TOTAL);
+    I.inner_its_max = (int)f(S_INNER_MAX);
+    I.relres_est = f(S_RELRES);
+    I.relres_true = f(S_TRUE_RES);
+    int st = GB_OK;
+    if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
+    else if (f(S_STATUS) != 0.0) st = GB_ERR_NOT_CONVERGED;
+    I.status = st;
+    if (st == GB_ERR_NONFINITE || (st != GB_OK && worst == GB_OK)) worst = st;
+  }
+  return worst;
+}
+
+}  // namespace
+
+void release_workspace(Ctx& c) {
+  Workspace& w = c.ws;
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
+                  w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
+                  w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (w.S_host) cudaFreeHost(w.S_host);
+  if (w.flag_host) cudaFreeHost(w.flag_host);
+  w = Workspace();
+}
+
+int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts& o, gb_info* info,
+          bool adjoint) {
+  if (!c.factored) fail(GB_ERR_INVALID_ARG, "factor_ic0 must succeed before solve");
+  if (k < 1 || k > 32) fail(GB_ERR_INVALID_ARG, "k must be in [1, 32]");
+  if (!rhs_dev || !x_dev || !info) fail(GB_ERR_INVALID_ARG, "null pointer argument");
+  if (!(o.tol >= 0.0) || !(o.inner_tol > 0.0) || o.max_outer < 1 || o.max_inner < 1)
+    fail(GB_ERR_INVALID_ARG, "bad solver options");
+  if (o.precision != GB_PREC_FP64 && o.precision != GB_PREC_MIXED) fail(GB_ERR_INVALID_ARG, "bad precision");
+  if (o.forced_inner_host && (k != 1 || o.nforced < 1 || o.nforced > (1 << 24)))
+    fail(GB_ERR_INVALID_ARG, "replay mode needs k == 1 and 1 <= nforced <= 2^24");
+  const int K = (k == 1) ? 1 : (k <= 8 ? 8 : 32);
+  ensure_workspace(c, K, o.precision, k);
+  Workspace& w = c.ws;
+  if (o.forced_inner_host) {
+    if ((size_t)o.nforced > w.forced_cap) {
+      if (w.forced) cudaFree(w.forced);
+      w.forced = (int32_t*)dmalloc(sizeof(int32_t) * o.nforced);
+      w.forced_cap = o.nforced;
+      w.graph_valid = false;
+    }
+    GBS_CUDA(cudaMemcpyAsync(w.forced, o.forced_inner_host, sizeof(int32_t) * o.nforced,
+                             cudaMemcpyHostToDevice, c.stream));
+  }
+  const double* rhs = rhs_dev;
+  if (adjoint) {
+    k_adjoint_coef<<<k, kBlock, 0, c.stream>>>((int)c.n_u, (int)c.n_p, k, rhs_dev, c.wmean.p, w.aux);
+    k_adjoint_rhs<<<grid_cap((c.n_u + c.n_p) * k), kBlock, 0, c.stream>>>((int)c.n_u, (int)c.n_p, k, rhs_dev,
+                                                                         c.wmean.p, w.aux, w.rhs_tmp);
+    GBS_CUDA(cudaGetLastError());
+    rhs = w.rhs_tmp;
+  }
+  const bool mixed = o.precision == GB_PREC_MIXED;
+  switch (K) {
+    case 1:
+      mixed ? dispatch_solve<1, float>(c, rhs, x_dev, k, o) : dispatch_solve<1, double>(c, rhs, x_dev, k, o);
+      break;
+    case 8:
+      mixed ? dispatch_solve<8, float>(c, rhs, x_dev, k, o) : dispatch_solve<8, double>(c, rhs, x_dev, k, o);
+      break;
+    default:
+      mixed ? dispatch_solve<32, float>(c, rhs, x_dev, k, o) : dispatch_solve<32, double>(c, rhs, x_dev, k, o);
+      break;
+  }
+  GBS_CUDA(cudaGetLastError());
+  return collect_info(c, k, info);
+}
+
+int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_solve_opts& o, gb_info* info) {
+  if (k < 1 || k > 32 || !rhs_host || !x_host) fail(GB_ERR_INVALID_ARG, "bad host solve arguments");
+  const int K = (k == 1) ? 1 : (k <= 8 ? 8 : 32);
+  ensure_workspace(c, K, o.precision, k);
+  const size_t bytes = sizeof(double) * (size_t)(c.n_u + c.n_p) * k;
+  GBS_CUDA(cudaMemcpyAsync(c.ws.host_in, rhs_host, bytes, cudaMemcpyHostToDevice, c.stream));
+  int st = solve(c, c.ws.host_in, c.ws.host_out, k, o, info, false);
+  GBS_CUDA(cudaMemcpyAsync(x_host, c.ws.host_out, bytes, cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  return st;
+}
+
+void apply_operator(Ctx& c, int which, const double* x, double* y) {
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble first");
+  if (which < 0 || which > 3 || !x || !y) fail(GB_ERR_INVALID_ARG, "bad operator request");
+  Args a = make_args(c, nullptr, 1);
+  const int64_t rows = which == 0 ? c.n_u + c.n_p : (which == 2 ? c.n_p : c.n_u);
+  k_apply_natural<<<grid_cap(rows * 8), kBlock, 0, c.stream>>>(a, which, x, y);
+  GBS_CUDA(cudaGetLastError());
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void dnu(Ctx& c, const double* lam, const double* x, int k, double* out) {
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble first");
+  if (k < 1 || k > 32 || !lam || !x || !out) fail(GB_ERR_INVALID_ARG, "bad dnu arguments");
+  ensure_workspace(c, c.ws.K > 0 ? c.ws.K : 1, c.ws.precision >= 0 ? c.ws.precision : 0, 0);
+  Args a = make_args(c, nullptr, 1);
+  const int grid = grid_cap(c.n_u * 8);
+  double* res = c.ws.aux + (size_t)kRB * 32 - 32;  // k results after the partials
+  k_dnu<<<grid, kBlock, 0, c.stream>>>(a, k, lam, x, c.ws.partial, c.ws.counter, res);
+  GBS_CUDA(cudaGetLastError());
+  GBS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+}  // namespace gbs

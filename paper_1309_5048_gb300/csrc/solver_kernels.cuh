@@ -1,0 +1,776 @@
+// solver_kernels.cuh -- kernels of the preconditioned MINRES solve (included by solver.cu only).
+//
+// Sec. 5: MINRES on K x = b, K = [A_h B^T; B 0], with the block-diagonal
+// preconditioner M = diag(M_A, M_Q) (eq. general_precond_M): M_A^{-1} r is a
+// relaxed inner conjugate-gradient solve with A_h preconditioned by IC(0)
+// (Sec. 6.4, "PCG(A)"), M_Q = Diag(Q_nu) with Q_nu = Q / (2 nu) (Sec. 5.1).
+// MINRES is the Lanczos process in the M^{-1} inner product with a QR
+// factorisation of the tridiagonal matrix by Givens rotations (eq.
+// opt_condition, eq. linsys_precond); |eta| tracks ||r||_{M^{-1}}.
+//
+// All arithmetic runs in the kernels below; the host only launches them.
+// Every reduction is written as per-block partials plus a last-block
+// epilogue that sums them in a fixed order and performs the scalar part of
+// the recurrence, so no scalar ever travels to the host inside a solve and
+// results do not depend on timing.  k right-hand sides run together in an
+// interleaved [n][K] layout; each keeps its own scalars and stops on its own
+// (masked), so every column follows the arithmetic of its own solve.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gbs_device.cuh"
+#include "gbs_internal.h"
+
+namespace gbs {
+
+namespace {
+
+constexpr int kRB = 304;  // blocks of the reduction kernels (2 per SM)
+
+struct Args {
+  int n_u, n_p, k;
+  // matrices (internal numbering)
+  const int32_t *A_ptr, *A_col;
+  const double* A_val;
+  const float* A_val32;
+  const int32_t *L_ptr, *L_col;
+  const double *L_val, *L_inv;
+  const float *L_val32, *L_inv32;
+  const int32_t *U_ptr, *U_col;
+  const double* U_val;
+  const float* U_val32;
+  const int32_t *B_ptr, *B_col, *Bt_ptr, *Bt_col;
+  const double *B_val, *Bt_val;
+  const double *Qdiag, *wmean;
+  const int32_t* order;
+  double nu;
+  // workspace
+  double *x, *V0, *V1, *V2, *Z0, *Z1, *W0, *W1, *W2, *q, *b;
+  void *cg_x, *cg_r, *cg_z, *cg_y, *cg_p, *cg_q;
+  double* S;
+  int* flag;
+  int* jcur;
+  const int32_t* forced;
+  int nforced;
+  double tol, inner_tol;
+  int max_outer, max_inner;
+  double* partial;
+  unsigned* counter;
+  cudaGraphConditionalHandle h_outer, h_inner;
+  int use_handles;
+};
+
+template <int K>
+struct Map {
+  static constexpr int G = (K == 1) ? 8 : K;  // lanes per row
+  static constexpr int RPW = 32 / G;          // rows per warp
+};
+
+__device__ __forceinline__ double& SF(const Args& a, int f, int t, int K) { return a.S[f * K + t]; }
+
+__device__ __forceinline__ double* Vbuf(const Args& a, int i) {
+  i %= 3;
+  return i == 0 ? a.V0 : (i == 1 ? a.V1 : a.V2);
+}
+__device__ __forceinline__ double* Wbuf(const Args& a, int i) {
+  i %= 3;
+  return i == 0 ? a.W0 : (i == 1 ? a.W1 : a.W2);
+}
+__device__ __forceinline__ double* Zbuf(const Args& a, int i) { return (i % 2) == 0 ? a.Z0 : a.Z1; }
+
+template <class T>
+__device__ __forceinline__ const T* pick(const double* d, const float* f);
+template <>
+__device__ __forceinline__ const double* pick<double>(const double* d, const float*) {
+  return d;
+}
+template <>
+__device__ __forceinline__ const float* pick<float>(const double*, const float* f) {
+  return f;
+}
+
+// ---------------------------------------------------------------- gather --
+// b (internal layout) from rhs [k][n] (natural numbering); zero the MINRES
+// vectors; ||b||^2 and a finiteness check per RHS; scalar initialisation.
+template <int K>
+__global__ void k_gather(Args a, const double* __restrict__ rhs) {
+  const int n = a.n_u + a.n_p;
+  double vals[2] = {0.0, 0.0};  // ||b||^2, nonfinite count
+  const int t = threadIdx.x % K;
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
+    double v = 0.0;
+    if (t < a.k) {
+      const int nat = r < a.n_u ? a.order[r] : r;
+      v = rhs[(size_t)t * n + nat];
+    }
+    const size_t idx = (size_t)r * K + t;
+    a.b[idx] = v;
+    a.x[idx] = 0.0;
+    a.V0[idx] = 0.0;
+    a.W0[idx] = 0.0;
+    a.W1[idx] = 0.0;
+    vals[0] += v * v;
+    if (!isfinite(v)) vals[1] += 1.0;
+  }
+  block_partials<K, 2>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K * 2];
+    finalize_partials<K, 2>(a.partial, gridDim.x, tot);
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      for (int f = 0; f < S_NFIELDS; ++f) SF(a, f, s, K) = 0.0;
+      const double bn = sqrt(tot[s * 2 + 0]);
+      SF(a, S_BNORM, s, K) = bn;
+      SF(a, S_NONFINITE, s, K) = tot[s * 2 + 1] > 0 ? 1.0 : 0.0;
+      const bool live = s < a.k && bn > 0.0 && tot[s * 2 + 1] == 0.0;
+      SF(a, S_OUTER_ACTIVE, s, K) = live ? 1.0 : 0.0;
+      SF(a, S_C, s, K) = 1.0;
+      SF(a, S_C_PREV, s, K) = 1.0;
+      SF(a, S_GAMMA_PREV, s, K) = 1.0;
+    }
+    if (threadIdx.x == 0) {
+      *a.jcur = 0;
+      *a.counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------ K-apply ----
+// y = K z_j for the live RHS, q = y / gamma_j (= K times the normalised z_j),
+// delta_j = q^T (z_j / gamma_j) = y^T z_j / gamma_j^2.
+template <int K>
+__global__ void k_stokes_apply(Args a) {
+  using M = Map<K>;
+  const int j = *a.jcur;
+  const double* __restrict__ z = Zbuf(a, j);
+  const int n = a.n_u + a.n_p;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % M::G;
+  const int t = (K == 1) ? 0 : g;
+  const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
+  const double ig = live ? 1.0 / SF(a, S_GAMMA, t, K) : 0.0;
+  double vals[1] = {0.0};
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
+  const int ng = (gridDim.x * blockDim.x) / M::G;
+  for (int r = gid; r < n; r += ng) {
+    double y = 0.0;
+    if (r < a.n_u) {
+      if (K == 1) {
+        for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += M::G) y += a.A_val[e] * z[a.A_col[e]];
+        for (int e = a.Bt_ptr[r] + g; e < a.Bt_ptr[r + 1]; e += M::G)
+          y += a.Bt_val[e] * z[a.n_u + a.Bt_col[e]];
+      } else {
+        for (int e = a.A_ptr[r]; e < a.A_ptr[r + 1]; ++e) y += a.A_val[e] * z[(size_t)a.A_col[e] * K + t];
+        for (int e = a.Bt_ptr[r]; e < a.Bt_ptr[r + 1]; ++e)
+          y += a.Bt_val[e] * z[(size_t)(a.n_u + a.Bt_col[e]) * K + t];
+      }
+    } else {
+      const int kr = r - a.n_u;
+      if (K == 1) {
+        for (int e = a.B_ptr[kr] + g; e < a.B_ptr[kr + 1]; e += M::G) y += a.B_val[e] * z[a.B_col[e]];
+      } else {
+        for (int e = a.B_ptr[kr]; e < a.B_ptr[kr + 1]; ++e) y += a.B_val[e] * z[(size_t)a.B_col[e] * K + t];
+      }
+    }
+    if (K == 1) y = group_sum<M::G>(y);
+    if (live && (K > 1 || g == 0)) {
+      const size_t idx = (size_t)r * K + t;
+      a.q[idx] = y * ig;
+      vals[0] += y * z[idx];
+    }
+  }
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
+        const double gm = SF(a, S_GAMMA, s, K);
+        SF(a, S_DELTA, s, K) = tot[s] / (gm * gm);
+      }
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// ----------------------------------------------------------- Lanczos -----
+// v_{j+1} = q - (delta_j/gamma_j) v_j - (gamma_j/gamma_{j-1}) v_{j-1}
+// (j = 0: v_1 = b).  The pressure block of z_{j+1} = M^{-1} v_{j+1} is
+// 2 nu v_p / diag(Q); the velocity block starts the inner CG with b = r =
+// v_{j+1,u}, x = 0.  Epilogue: ||b_u|| and the inner CG state per RHS.
+template <int K, class T>
+__global__ void k_lanczos(Args a) {
+  const int j = *a.jcur;
+  const int n = a.n_u + a.n_p;
+  double* __restrict__ vn = Vbuf(a, j + 1);
+  const double* __restrict__ vc = Vbuf(a, j);
+  const double* __restrict__ vp = Vbuf(a, j + 2);  // (j - 1) mod 3
+  double* __restrict__ zn = Zbuf(a, j + 1);
+  T* __restrict__ r_cg = (T*)a.cg_r;
+  T* __restrict__ x_cg = (T*)a.cg_x;
+  const int t = threadIdx.x % K;
+  const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
+  double c1 = 0.0, c2 = 0.0;
+  if (live && j > 0) {
+    const double gm = SF(a, S_GAMMA, t, K);
+    c1 = SF(a, S_DELTA, t, K) / gm;
+    c2 = gm / SF(a, S_GAMMA_PREV, t, K);
+  }
+  double vals[1] = {0.0};
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
+    if (!live) continue;
+    const size_t idx = (size_t)r * K + t;
+    const double v = (j == 0) ? a.b[idx] : a.q[idx] - c1 * vc[idx] - c2 * vp[idx];
+    vn[idx] = v;
+    if (r < a.n_u) {
+      r_cg[idx] = (T)v;
+      x_cg[idx] = (T)0;
+      vals[0] += v * v;
+    } else {
+      zn[idx] = 2.0 * a.nu * v / a.Qdiag[r - a.n_u];
+    }
+  }
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    int any = 0;
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      SF(a, S_CG_ACTIVE, s, K) = 0.0;
+      if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
+        const double bn = sqrt(tot[s]);
+        SF(a, S_CG_BNORM, s, K) = bn;
+        SF(a, S_CG_ITS, s, K) = 0.0;
+        double target = -1.0;
+        if (a.forced) {
+          const int app = (int)SF(a, S_APPS, s, K);
+          target = app < a.nforced ? (double)a.forced[app] : 0.0;
+        }
+        SF(a, S_CG_TARGET, s, K) = target;
+        SF(a, S_APPS, s, K) += 1.0;
+        const bool act = bn > 0.0 && target != 0.0;
+        SF(a, S_CG_ACTIVE, s, K) = act ? 1.0 : 0.0;
+        any = act;
+      }
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+      a.flag[1] = any;
+      if (a.use_handles) cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+      *a.counter = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------- gamma/Givens --
+// z_{j+1,u} = x_cg (the inner CG result); gamma_{j+1}^2 = z_{j+1}^T v_{j+1}.
+// j = 0: initial recurrence values.  j >= 1: Givens rotation of the new
+// column of the tridiagonal matrix, coefficient of the x update, new eta and
+// the convergence test |eta| / gamma_1 <= tol.
+template <int K, class T>
+__global__ void k_gamma(Args a) {
+  const int j = *a.jcur;
+  const int n = a.n_u + a.n_p;
+  const double* __restrict__ vn = Vbuf(a, j + 1);
+  double* __restrict__ zn = Zbuf(a, j + 1);
+  const T* __restrict__ x_cg = (const T*)a.cg_x;
+  const int t = threadIdx.x % K;
+  const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
+  double vals[1] = {0.0};
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
+    if (!live) continue;
+    const size_t idx = (size_t)r * K + t;
+    double z;
+    if (r < a.n_u) {
+      z = (double)x_cg[idx];
+      zn[idx] = z;
+    } else {
+      z = zn[idx];
+    }
+    vals[0] += z * vn[idx];
+  }
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    int any = 0;
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
+        const double gg = tot[s];
+        bool stop = false;
+        if (!isfinite(gg)) {
+          SF(a, S_NONFINITE, s, K) = 1.0;
+          stop = true;
+        } else if (gg < 0.0) {
+          SF(a, S_STATUS, s, K) = 2.0;  // preconditioner not positive
+          stop = true;
+        }
+        const double gnext = stop ? 0.0 : sqrt(gg);
+        if (j == 0) {
+          SF(a, S_GAMMA, s, K) = gnext;
+          SF(a, S_GAMMA1, s, K) = gnext;
+          SF(a, S_ETA, s, K) = gnext;
+          SF(a, S_XCOEF, s, K) = 0.0;
+          if (stop || gnext == 0.0) {
+            SF(a, S_OUTER_ACTIVE, s, K) = 0.0;
+          }
+        } else {
+          const double gm = SF(a, S_GAMMA, s, K), gp = SF(a, S_GAMMA_PREV, s, K);
+          const double dl = SF(a, S_DELTA, s, K);
+          const double c = SF(a, S_C, s, K), cp = SF(a, S_C_PREV, s, K);
+          const double sn = SF(a, S_S, s, K), sp = SF(a, S_S_PREV, s, K);
+          (void)gp;
+          const double a0 = c * dl - cp * sn * gm;
+          const double a1 = sqrt(a0 * a0 + gnext * gnext);
+          const double a2 = sn * dl + cp * c * gm;
+          const double a3 = sp * gm;
+          const double cn = a0 / a1, snn = gnext / a1;
+          const double eta = SF(a, S_ETA, s, K);
+          SF(a, S_A1, s, K) = a1;
+          SF(a, S_A2, s, K) = a2;
+          SF(a, S_A3, s, K) = a3;
+          SF(a, S_XCOEF, s, K) = cn * eta;
+          SF(a, S_ETA, s, K) = -snn * eta;
+          SF(a, S_C_PREV, s, K) = c;
+          SF(a, S_C, s, K) = cn;
+          SF(a, S_S_PREV, s, K) = sn;
+          SF(a, S_S, s, K) = snn;
+          SF(a, S_GAMMA_PREV, s, K) = gm;
+          SF(a, S_GAMMA, s, K) = gnext;
+          SF(a, S_OUTER_ITS, s, K) = j;
+          const double rel = fabs(-snn * eta) / SF(a, S_GAMMA1, s, K);
+          SF(a, S_RELRES, s, K) = rel;
+          // S_OUTER_ACTIVE stays set until k_update has applied this step
+          SF(a, S_STATUS, s, K) = (rel <= a.tol || stop) ? (stop ? SF(a, S_STATUS, s, K) : 0.0) : 1.0;
+          if (!isfinite(a1) || !isfinite(rel)) SF(a, S_NONFINITE, s, K) = 1.0;
+        }
+      }
+      any = SF(a, S_OUTER_ACTIVE, s, K) != 0.0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+      if (j == 0) {
+        *a.jcur = 1;
+        a.flag[0] = any;
+        if (a.use_handles) cudaGraphSetConditional(a.h_outer, any ? 1u : 0u);
+      }
+      *a.counter = 0;
+    }
+  }
+}
+
+// w_{j+1} = (z_j / gamma_j - a3 w_{j-1} - a2 w_j) / a1;  x += (c_{j+1} eta_j) w_{j+1}.
+// gamma_j here is the value before k_gamma advanced it, i.e. S_GAMMA_PREV.
+// Epilogue: retire converged RHS, advance j, set the outer loop condition.
+template <int K>
+__global__ void k_update(Args a) {
+  const int j = *a.jcur;
+  const int n = a.n_u + a.n_p;
+  const double* __restrict__ zc = Zbuf(a, j);
+  const double* __restrict__ wp = Wbuf(a, j + 2);  // w_{j-1}
+  const double* __restrict__ wc = Wbuf(a, j);      // w_j
+  double* __restrict__ wn = Wbuf(a, j + 1);        // w_{j+1}
+  const int t = threadIdx.x % K;
+  const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
+  double ig = 0, a1i = 0, a2 = 0, a3 = 0, xc = 0;
+  if (live) {
+    ig = 1.0 / SF(a, S_GAMMA_PREV, t, K);
+    a1i = 1.0 / SF(a, S_A1, t, K);
+    a2 = SF(a, S_A2, t, K);
+    a3 = SF(a, S_A3, t, K);
+    xc = SF(a, S_XCOEF, t, K);
+  }
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
+    if (!live) continue;
+    const size_t idx = (size_t)r * K + t;
+    const double w = (zc[idx] * ig - a3 * wp[idx] - a2 * wc[idx]) * a1i;
+    wn[idx] = w;
+    a.x[idx] += xc * w;
+  }
+  if (last_block(a.counter)) {
+    int any = 0;
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
+        const bool conv = SF(a, S_STATUS, s, K) != 1.0;
+        const bool cap = j >= a.max_outer;
+        const bool bad = SF(a, S_NONFINITE, s, K) != 0.0;
+        if (conv || cap || bad) SF(a, S_OUTER_ACTIVE, s, K) = 0.0;
+      }
+      any = SF(a, S_OUTER_ACTIVE, s, K) != 0.0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+      *a.jcur = j + 1;
+      a.flag[0] = any;
+      if (a.use_handles) cudaGraphSetConditional(a.h_outer, any ? 1u : 0u);
+      *a.counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------- inner CG --
+// q = A p and p^T q; epilogue alpha = rho / p^T q.
+template <int K, class T>
+__global__ void k_cg_spmv(Args a) {
+  using M = Map<K>;
+  const T* __restrict__ val = pick<T>(a.A_val, a.A_val32);
+  const T* __restrict__ p = (const T*)a.cg_p;
+  T* __restrict__ q = (T*)a.cg_q;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % M::G;
+  const int t = (K == 1) ? 0 : g;
+  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
+  double vals[1] = {0.0};
+  if (K == 1 && !live) {
+    // nothing to do for this RHS; still take part in the reduction
+  } else {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
+    const int ng = (gridDim.x * blockDim.x) / M::G;
+    for (int r = gid; r < a.n_u; r += ng) {
+      T y = 0;
+      if (K == 1) {
+        for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += M::G) y += val[e] * p[a.A_col[e]];
+        if (sizeof(T) == 8) y = (T)group_sum<M::G>((double)y);
+        else y = (T)group_sumf<M::G>((float)y);
+      } else {
+        for (int e = a.A_ptr[r]; e < a.A_ptr[r + 1]; ++e) y += val[e] * p[(size_t)a.A_col[e] * K + t];
+      }
+      if (live && (K > 1 || g == 0)) {
+        const size_t idx = (size_t)r * K + t;
+        q[idx] = y;
+        vals[0] += (double)y * (double)p[idx];
+      }
+    }
+  }
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) SF(a, S_ALPHA, s, K) = SF(a, S_RHO, s, K) / tot[s];
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2; epilogue: stopping test
+// ||r|| <= inner_tol ||b|| or its == max_inner (or the replayed count).
+template <int K, class T>
+__global__ void k_cg_axpy(Args a) {
+  const T* __restrict__ p = (const T*)a.cg_p;
+  const T* __restrict__ q = (const T*)a.cg_q;
+  T* __restrict__ x = (T*)a.cg_x;
+  T* __restrict__ r = (T*)a.cg_r;
+  const int t = threadIdx.x % K;
+  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
+  const T alpha = live ? (T)SF(a, S_ALPHA, t, K) : (T)0;
+  double vals[1] = {0.0};
+  T acc = 0;
+  const int stride = (gridDim.x * blockDim.x) / K;
+  if (live) {
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+      const size_t idx = (size_t)i * K + t;
+      x[idx] += alpha * p[idx];
+      const T rv = r[idx] - alpha * q[idx];
+      r[idx] = rv;
+      acc += rv * rv;
+    }
+  }
+  vals[0] = (double)acc;
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    int any = 0;
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) {
+        const double its = SF(a, S_CG_ITS, s, K) + 1.0;
+        SF(a, S_CG_ITS, s, K) = its;
+        SF(a, S_INNER_TOTAL, s, K) += 1.0;
+        const double rn = sqrt(tot[s]);
+        SF(a, S_RNORM, s, K) = rn;
+        const double target = SF(a, S_CG_TARGET, s, K);
+        bool stop;
+        if (target >= 0.0) stop = its >= target;
+        else stop = rn <= a.inner_tol * SF(a, S_CG_BNORM, s, K) || its >= a.max_inner || !isfinite(rn);
+        if (stop) {
+          SF(a, S_CG_ACTIVE, s, K) = 0.0;
+          if (its > SF(a, S_INNER_MAX, s, K)) SF(a, S_INNER_MAX, s, K) = its;
+        }
+      }
+      any = SF(a, S_CG_ACTIVE, s, K) != 0.0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+      a.flag[1] = any;
+      if (a.use_handles) cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+      *a.counter = 0;
+    }
+  }
+}
+
+// One level of a triangular solve, rows [r0, r1) of the internal numbering:
+//   forward  (L):   y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii
+//   backward (L^T): z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii
+// The rows of a level depend only on rows of earlier (forward) or later
+// (backward) levels, which earlier launches have finished.
+template <int K, class T, bool FWD>
+__global__ void k_trsv_level(Args a, int r0, int r1) {
+  using M = Map<K>;
+  const int32_t* __restrict__ ptr = FWD ? a.L_ptr : a.U_ptr;
+  const int32_t* __restrict__ col = FWD ? a.L_col : a.U_col;
+  const T* __restrict__ val = FWD ? pick<T>(a.L_val, a.L_val32) : pick<T>(a.U_val, a.U_val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* __restrict__ rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* __restrict__ out = (T*)(FWD ? a.cg_y : a.cg_z);
+  const int lane = threadIdx.x & 31;
+  const int g = lane % M::G;
+  const int t = (K == 1) ? 0 : g;
+  if (SF(a, S_CG_ACTIVE, t, K) == 0.0) return;  // uniform per group of lanes
+  const int row = r0 + (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
+  if (row >= r1) return;
+  T s = 0;
+  if (K == 1) {
+    for (int e = ptr[row] + g; e < ptr[row + 1]; e += M::G) s += val[e] * out[col[e]];
+    if (sizeof(T) == 8) s = (T)group_sum<M::G>((double)s);
+    else s = (T)group_sumf<M::G>((float)s);
+    if (g == 0) out[row] = (rhs[row] - s) * inv[row];
+  } else {
+    for (int e = ptr[row]; e < ptr[row + 1]; ++e) s += val[e] * out[(size_t)col[e] * K + t];
+    const size_t idx = (size_t)row * K + t;
+    out[idx] = (rhs[idx] - s) * inv[row];
+  }
+}
+
+// rho = r^T z.  init: p = z, rho.  Otherwise beta = rho_new / rho.
+template <int K, class T>
+__global__ void k_cg_rho(Args a, int init) {
+  const T* __restrict__ r = (const T*)a.cg_r;
+  const T* __restrict__ z = (const T*)a.cg_z;
+  T* __restrict__ p = (T*)a.cg_p;
+  const int t = threadIdx.x % K;
+  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
+  double vals[1] = {0.0};
+  T acc = 0;
+  const int stride = (gridDim.x * blockDim.x) / K;
+  if (live) {
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+      const size_t idx = (size_t)i * K + t;
+      const T zv = z[idx];
+      acc += r[idx] * zv;
+      if (init) p[idx] = zv;
+    }
+  }
+  vals[0] = (double)acc;
+  block_partials<K, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) {
+        if (init) {
+          SF(a, S_RHO, s, K) = tot[s];
+        } else {
+          SF(a, S_ALPHA, s, K) = tot[s] / SF(a, S_RHO, s, K);  // beta, consumed by k_cg_pupdate
+          SF(a, S_RHO, s, K) = tot[s];
+        }
+      }
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// p = z + beta p (beta kept in S_ALPHA between k_cg_rho and this kernel).
+template <int K, class T>
+__global__ void k_cg_pupdate(Args a) {
+  const T* __restrict__ z = (const T*)a.cg_z;
+  T* __restrict__ p = (T*)a.cg_p;
+  const int t = threadIdx.x % K;
+  if (SF(a, S_CG_ACTIVE, t, K) == 0.0) return;
+  const T beta = (T)SF(a, S_ALPHA, t, K);
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+    const size_t idx = (size_t)i * K + t;
+    p[idx] = z[idx] + beta * p[idx];
+  }
+}
+
+// --------------------------------------------------------------- exit ----
+// r = b - K x: ||r||^2, w^T x_p and w^T 1 for the zero-mean filter.
+template <int K>
+__global__ void k_residual(Args a) {
+  using M = Map<K>;
+  const double* __restrict__ x = a.x;
+  const int n = a.n_u + a.n_p;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % M::G;
+  const int t = (K == 1) ? 0 : g;
+  double vals[3] = {0.0, 0.0, 0.0};
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
+  const int ng = (gridDim.x * blockDim.x) / M::G;
+  for (int r = gid; r < n; r += ng) {
+    double y = 0.0;
+    if (r < a.n_u) {
+      if (K == 1) {
+        for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += M::G) y += a.A_val[e] * x[a.A_col[e]];
+        for (int e = a.Bt_ptr[r] + g; e < a.Bt_ptr[r + 1]; e += M::G) y += a.Bt_val[e] * x[a.n_u + a.Bt_col[e]];
+      } else {
+        for (int e = a.A_ptr[r]; e < a.A_ptr[r + 1]; ++e) y += a.A_val[e] * x[(size_t)a.A_col[e] * K + t];
+        for (int e = a.Bt_ptr[r]; e < a.Bt_ptr[r + 1]; ++e)
+          y += a.Bt_val[e] * x[(size_t)(a.n_u + a.Bt_col[e]) * K + t];
+      }
+    } else {
+      const int kr = r - a.n_u;
+      if (K == 1) {
+        for (int e = a.B_ptr[kr] + g; e < a.B_ptr[kr + 1]; e += M::G) y += a.B_val[e] * x[a.B_col[e]];
+      } else {
+        for (int e = a.B_ptr[kr]; e < a.B_ptr[kr + 1]; ++e) y += a.B_val[e] * x[(size_t)a.B_col[e] * K + t];
+      }
+    }
+    if (K == 1) y = group_sum<M::G>(y);
+    if (K > 1 || g == 0) {
+      const size_t idx = (size_t)r * K + t;
+      const double res = a.b[idx] - y;
+      vals[0] += res * res;
+      if (r >= a.n_u) {
+        vals[1] += a.wmean[r - a.n_u] * x[idx];
+        vals[2] += a.wmean[r - a.n_u];
+      }
+    }
+  }
+  block_partials<K, 3>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[K * 3];
+    finalize_partials<K, 3>(a.partial, gridDim.x, tot);
+    if (threadIdx.x < K) {
+      const int s = threadIdx.x;
+      const double bn = SF(a, S_BNORM, s, K);
+      SF(a, S_TRUE_RES, s, K) = bn > 0.0 ? sqrt(tot[s * 3]) / bn : 0.0;
+      SF(a, S_PMEAN, s, K) = tot[s * 3 + 2] != 0.0 ? tot[s * 3 + 1] / tot[s * 3 + 2] : 0.0;
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// out [k][n] (natural numbering) from x; pressure shifted to zero mean.
+template <int K>
+__global__ void k_scatter(Args a, double* __restrict__ out) {
+  const int n = a.n_u + a.n_p;
+  const int t = threadIdx.x % K;
+  if (t >= a.k) return;
+  const double pm = SF(a, S_PMEAN, t, K);
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
+    const size_t idx = (size_t)r * K + t;
+    if (r < a.n_u) out[(size_t)t * n + a.order[r]] = a.x[idx];
+    else out[(size_t)t * n + r] = a.x[idx] - pm;
+  }
+}
+
+// Adjoint right-hand side: the pressure part of dL/d(filtered p) is mapped by
+// P^T, P = I - 1 w^T / (w^T 1):  P^T g = g - w (1^T g) / (w^T 1).
+__global__ void k_adjoint_coef(int n_u, int n_p, int k, const double* __restrict__ g,
+                               const double* __restrict__ w, double* __restrict__ coef) {
+  __shared__ double s1[kBlock], s2[kBlock];
+  const int t = blockIdx.x;
+  if (t >= k) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_p; i += blockDim.x) {
+    a += g[(size_t)t * (n_u + n_p) + n_u + i];
+    b += w[i];
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) coef[t] = s1[0] / s2[0];
+}
+
+__global__ void k_adjoint_rhs(int n_u, int n_p, int k, const double* __restrict__ g,
+                              const double* __restrict__ w, const double* __restrict__ coef,
+                              double* __restrict__ out) {
+  const size_t n = (size_t)n_u + n_p, total = n * k;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = i / n, r = i % n;
+    out[i] = r < (size_t)n_u ? g[i] : g[i] - w[r - n_u] * coef[t];
+  }
+}
+
+// Operators in natural numbering (one vector, FP64):
+// which 0: y = K x; 1: y = A x_u; 2: y = B x_u; 3: y = B^T x_p.
+__global__ void k_apply_natural(Args a, int which, const double* __restrict__ xin, double* __restrict__ yout) {
+  const int lane = threadIdx.x & 31, g = lane & 7;
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, ng = (gridDim.x * blockDim.x) >> 3;
+  const int nu = a.n_u;
+  const int rows = (which == 0) ? nu + a.n_p : (which == 2 ? a.n_p : nu);
+  const double* xu = xin;
+  const double* xp = (which == 0) ? xin + nu : xin;
+  for (int r = gid; r < rows; r += ng) {
+    double y = 0.0;
+    int out_index;
+    if ((which == 0 && r < nu) || which == 1 || which == 3) {
+      if (which != 3)
+        for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += 8) y += a.A_val[e] * xu[a.order[a.A_col[e]]];
+      if (which != 1)
+        for (int e = a.Bt_ptr[r] + g; e < a.Bt_ptr[r + 1]; e += 8) y += a.Bt_val[e] * xp[a.Bt_col[e]];
+      out_index = a.order[r];
+    } else {
+      const int kr = (which == 0) ? r - nu : r;
+      for (int e = a.B_ptr[kr] + g; e < a.B_ptr[kr + 1]; e += 8) y += a.B_val[e] * xu[a.order[a.B_col[e]]];
+      out_index = (which == 0) ? r : kr;
+    }
+    y = group_sum<8>(y);
+    if (g == 0) yout[out_index] = y;
+  }
+}
+
+// dL/dnu = -lam_u^T A_h u / nu for each RHS (natural-numbered inputs [k][n]).
+__global__ void k_dnu(Args a, int k, const double* __restrict__ lam, const double* __restrict__ xv,
+                      double* __restrict__ partial, unsigned* counter, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, g = lane & 7;
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, ng = (gridDim.x * blockDim.x) >> 3;
+  const size_t n = (size_t)a.n_u + a.n_p;
+  for (int t = 0; t < k; ++t) {
+    double vals[1] = {0.0};
+    const double* u = xv + (size_t)t * n;
+    const double* l = lam + (size_t)t * n;
+    for (int r = gid; r < a.n_u; r += ng) {
+      double y = 0.0;
+      for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += 8) y += a.A_val[e] * u[a.order[a.A_col[e]]];
+      y = group_sum<8>(y);
+      if (g == 0) vals[0] += l[a.order[r]] * y;
+    }
+    block_partials<1, 1>(vals, partial + (size_t)t * gridDim.x);
+  }
+  if (last_block(counter)) {
+    __shared__ double tot[1];
+    for (int t = 0; t < k; ++t) {
+      finalize_partials<1, 1>(partial + (size_t)t * gridDim.x, gridDim.x, tot);
+      if (threadIdx.x == 0) out[t] = -tot[0] / a.nu;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+}  // namespace
+
+}  // namespace gbs
