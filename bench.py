@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Stokes solver: solves/s at relres 1e-8.
+
+One step = one complete solve of the workload (gather, preconditioned MINRES
+with the inner IC(0)-CG preconditioner, true residual, zero-mean pressure
+filter, scatter) on inputs already resident in HBM.  The problem set-up
+(patterns, assembly, IC(0) factorisation) is done once before the timed
+region, like the paper's separate R+F column.
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbs|reference]
+                  [--workload 2d256|2d256p4|2d16|3d32|2d1024|3d48]
+Under torchrun (N > 1) each rank solves its own forcings on its own GPU
+(replicas: the method has no data-parallel exchange); the value is the total
+number of solves over the slowest rank's time.  --impl reference times the
+FP64 CPU oracle (the only other implementation there is) on bounded samples.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Stokes solves/s at relres 1e-8, plain FP64 vs mixed/batched; SpMV HBM GB/s"
+
+WORKLOADS = {
+    "2d256": dict(dim=2, N=256, p=3, desc="2D unit square, 256x256 elements, velocity degree 3 / pressure degree 2 "
+                                          "(k'=2), nu=1, Nitsche no-slip, 16-mode seeded Fourier forcing"),
+    "2d256p4": dict(dim=2, N=256, p=4, desc="2D unit square, 256x256 elements, k'=3, nu=1, 16-mode Fourier forcing"),
+    "2d16": dict(dim=2, N=16, p=3, desc="2D unit square, 16x16 elements, k'=2, nu=1, 16-mode Fourier forcing"),
+    "3d32": dict(dim=3, N=32, p=3, desc="3D unit cube, 32^3 elements, k'=2, nu=1, 16-mode Fourier forcing"),
+    "2d1024": dict(dim=2, N=1024, p=3, desc="2D unit square, 1024x1024 elements, k'=2, nu=1, Fourier forcing"),
+    "3d48": dict(dim=3, N=48, p=3, desc="3D unit cube, 48^3 elements, k'=2, nu=1, Fourier forcing"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d256")
+    ap.add_argument("--ordering", choices=["natural", "rcm", "multicolour"], default="multicolour")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--k", type=int, default=1, help="right-hand sides per solve")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--max-outer", type=int, default=5000,
+                    help="MINRES iteration cap (lowered only for short profiling runs)")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    return a
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1309_5048_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("src_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(s, kernel, precision, k):
+    """Bytes the method must move per launch (each stored nonzero read once
+    as value + 32-bit index, each vector operand read or written once)."""
+    vb = 4 if precision == "mixed" else 8
+    mb = vb + 4
+    nnzL = s.nnzL  # includes the diagonal (stored as its inverse)
+    if kernel == "cg_spmv":  # q = A p, p^T q: matrix + p gather + q write + row pointers
+        return mb * s.nnzA + k * (2 * vb) * s.n_u + 4 * s.n_u
+    if kernel == "ic0_apply":  # L y = r then L^T z = y
+        one = mb * nnzL + k * (2 * vb) * s.n_u + 4 * s.n_u
+        return 2 * one
+    if kernel == "stokes_apply":  # A, B^T, B in FP64 + z gather + q write
+        return 12 * (s.nnzA + 2 * s.nnzB) + k * 16 * s.n + 4 * (s.n_u + s.n)
+    raise ValueError(kernel)
+
+
+def launches_per_solve(s, info):
+    """Kernel launches of one solve as the graph driver issues them."""
+    L = s.nlevels
+    return (4 + 3 * info["outer_its"] + info["precond_apps"] * (2 * L + 2)
+            + info["inner_its_total"] * (2 * L + 4))
+
+
+def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of one
+    solve: the first m MINRES iterations, extrapolated to the full solve."""
+    import numpy as np
+
+    import oracle
+    from paper_1309_5048_gb300.inputs import fourier_modes
+    P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=ordering)
+    P.factor()
+    kappa, amp = fourier_modes(W["dim"], seed=0)
+    b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
+    t = time.perf_counter()
+    P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2)
+    pilot = (time.perf_counter() - t) / 2
+    m = int(max(2, min(outer_full, target_s / max(pilot, 1e-6))))
+    t = time.perf_counter()
+    _, info = P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=m)
+    dt = time.perf_counter() - t
+    per_outer = dt / max(info["outer"], 1)
+    est = per_outer * max(outer_full, 1)
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d MINRES iterations of one solve (forcing seed 0), %.1f s, "
+                      "extrapolated linearly to the full solve; oracle assembly/ordering/IC(0) excluded"
+                      % (info["outer"], outer_full, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle, each step a bounded sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1309_5048_gb300.inputs import fourier_modes
+    W = WORKLOADS[args.workload]
+    P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=args.ordering)
+    P.factor()
+    kappa, amp = fourier_modes(W["dim"], seed=0)
+    b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
+    # one untimed full solve gives the outer count used to extrapolate samples
+    t = time.perf_counter()
+    x, full = P.minres(b, tol=args.tol, inner_tol=args.inner_tol)
+    t_full = time.perf_counter() - t
+    outer_full = max(full["outer"], 1)
+    per_outer_full = t_full / outer_full
+    m = int(max(1, min(outer_full, 4.0 / max(per_outer_full, 1e-6))))  # ~4 s per step
+    for _ in range(args.warmup):
+        P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _, info = P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m)
+    dt = time.perf_counter() - t
+    per_solve = dt / args.steps / max(info["outer"], 1) * outer_full
+    value = 1.0 / per_solve
+    sample = ("each step: first %d of %d MINRES iterations of one solve (seed 0), extrapolated; "
+              "one untimed full solve took %.1f s" % (info["outer"], outer_full, t_full))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["desc"], "ordering": args.ordering, "k": 1, "tol": args.tol,
+                       "inner_tol": args.inner_tol},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "outer_its": outer_full, "relres_true": full["relres_true"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_1309_5048_gb300 as gb
+    from paper_1309_5048_gb300.inputs import fourier_modes
+    W = WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    s = gb.Stokes(W["dim"], W["N"], W["p"], ordering=args.ordering)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.assemble(1.0)
+    s.factor_ic0()
+    torch.cuda.synchronize()
+    t_rf = time.perf_counter() - t0
+    k = args.k
+
+    def make_rhs(k, seed0):
+        rhs = torch.zeros(k, s.n, dtype=torch.float64, device="cuda")
+        for t in range(k):
+            kap, amp = fourier_modes(W["dim"], seed=seed0 + t)
+            rhs[t, : s.n_u] = s.load_fourier(kap, amp)
+        return rhs
+
+    rhs = make_rhs(k, rank * 1000)
+    out = torch.empty_like(rhs)
+    opts = dict(tol=args.tol, inner_tol=args.inner_tol, precision=args.precision, use_graph=not args.no_graph,
+                max_outer=args.max_outer)
+
+    def timed(rhs_, out_, steps, warmup, **o):
+        info = None
+        for _ in range(warmup):
+            _, info = s.solve(rhs_, out=out_, **o)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            _, info = s.solve(rhs_, out=out_, **o)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1), info
+
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        _, info = s.solve(rhs, out=out, **opts)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        _, info = s.solve(rhs, out=out, **opts)
+    e1.record()
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    infos = info if isinstance(info, list) else [info]
+    value = world * args.steps * k / (ms / 1000.0)
+
+    # end to end through the public host-buffer call (pinned memory)
+    rhs_h = rhs.cpu().pin_memory()
+    out_h = torch.empty_like(rhs_h).pin_memory()
+    for _ in range(2):
+        s.solve_host(rhs_h, out_h, **opts)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        s.solve_host(rhs_h, out_h, **opts)
+    e2e_s = time.perf_counter() - t
+    if dist is not None:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    bytes_io = 8 * k * s.n
+
+    # per-kernel timing (events on the library's stream) and the roofline
+    x_last = out.clone()
+    _, info1 = s.solve(rhs, out=out, **opts)
+    inf0 = info1[0] if isinstance(info1, list) else info1
+    kern = {}
+    for name, reps in (("cg_spmv", 50), ("ic0_apply", 20), ("stokes_apply", 50)):
+        ms_k = s.time_kernel(name, reps)
+        ab = algorithmic_bytes(s, name, args.precision, k)
+        kern[name] = {"ms_per_launch": ms_k, "algorithmic_bytes": ab, "gbs": ab / (ms_k * 1e-3) / 1e9}
+    count = {"cg_spmv": inf0["inner_its_total"], "ic0_apply": inf0["precond_apps"] + inf0["inner_its_total"],
+             "stokes_apply": inf0["outer_its"] + 1}
+    for name in kern:
+        kern[name]["launches_per_solve"] = count[name]
+        kern[name]["est_ms_per_solve"] = count[name] * kern[name]["ms_per_launch"]
+    dom = max(kern, key=lambda n: kern[n]["est_ms_per_solve"])
+    peak, peak_kind = measured_peak()
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / peak, "peak_source": peak_kind,
+            "traffic": traffic_for(dom, args.workload),
+            "unit_of_launch": ("one preconditioner application: forward + backward IC(0) sweep over %d levels "
+                               "each" % s.nlevels) if dom == "ic0_apply" else "one kernel launch"}
+    del x_last
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for name, prec, kk in (("mixed_k1", "mixed", 1), ("fp64_k32", "fp64", 32), ("mixed_k32", "mixed", 32)):
+            r = make_rhs(kk, 5000)
+            o = torch.empty_like(r)
+            st = 1 if kk > 1 else max(1, args.steps // 2)
+            ms_v, inf_v = timed(r, o, st, 1, tol=args.tol, inner_tol=args.inner_tol, precision=prec,
+                                use_graph=not args.no_graph)
+            iv = inf_v if isinstance(inf_v, list) else [inf_v]
+            variants[name] = {"solves_per_s": st * kk / (ms_v / 1000.0), "k": kk, "precision": prec,
+                              "outer_its_mean": statistics.mean(i["outer_its"] for i in iv),
+                              "inner_its_mean": statistics.mean(i["inner_its_total"] for i in iv),
+                              "relres_true_max": max(i["relres_true"] for i in iv)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(W, args.ordering, args.tol, args.inner_tol, int(infos[0]["outer_its"]))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": W["desc"], "ordering": args.ordering, "k": k, "precision": args.precision,
+                       "tol": args.tol, "inner_tol": args.inner_tol, "graph": not args.no_graph,
+                       "l2": "no flush: per-iteration working set (A, L, L^T, vectors) exceeds the 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * args.steps * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": int(args.steps * sum(launches_per_solve(s, i) for i in infos)),
+            "clocks": clock_info,
+            "outer_its": infos[0]["outer_its"], "inner_its_total": infos[0]["inner_its_total"],
+            "inner_its_mean": infos[0]["inner_its_total"] / max(infos[0]["precond_apps"], 1),
+            "relres_est": infos[0]["relres_est"], "relres_true": infos[0]["relres_true"],
+            "setup_s": t_setup, "assemble_factor_s": t_rf, "levels": s.nlevels,
+            "kernels": kern, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -49,7 +49,8 @@ extern "C" {
 #define GB_ERR_IC0_BREAKDOWN 4  /* IC(0) met a non-positive pivot */
 #define GB_ERR_NOT_CONVERGED 5  /* iteration cap reached; outputs written */
 #define GB_ERR_NONFINITE 6      /* NaN/Inf met in the right-hand side or iterates */
-#define GB_ERR_DEVICE_TIMEOUT 7 /* a bounded device wait gave up */
+#define GB_ERR_DEVICE_TIMEOUT 7 /* reserved: a bounded device wait gave up (no kernel
+                                   of this version waits on another one) */
 
 /* Orderings of A_h applied before IC(0).  The paper reorders A by reverse
  * Cuthill-McKee (Sec. 6.4); natural and multicolour orderings are offered
@@ -172,6 +173,19 @@ int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, doubl
  * y_u = B^T x_p (which = 3), all in natural numbering, FP64, one vector.
  * x_dev / y_dev sizes follow the operator. */
 int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
+
+/* Benchmark instrumentation.  Times `reps` (>= 1) launches of one kernel
+ * family of the most recent gb_solve, with the same batch width, precision
+ * and launch configuration, on the context's stream with CUDA events, after
+ * one untimed launch; *ms_host receives the mean milliseconds per launch.
+ *  which 0: inner CG product q = A p with its p^T q reduction (one kernel)
+ *        1: one IC(0) preconditioner application, forward then backward
+ *           triangular solve over all levels (2 x levels launches)
+ *        2: Stokes operator product K z with its reduction (one kernel)
+ *        3: forward triangular solve over all levels (levels launches)
+ * The buffers of the last solve are reused and overwritten (its returned
+ * solution is not touched).  GB_ERR_INVALID_ARG before any solve. */
+int gb_time_kernel(gb_ctx* ctx, int which, int reps, double* ms_host);
 
 /* Copies internal arrays to the host for inspection and parity tests.
  *  what 0: A_h CSR in natural numbering: rowptr int64 [n_u+1], col int32,

@@ -53,7 +53,7 @@ class gb_info(C.Structure):
 
 EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
-            "gb_export", "gb_destroy", "gb_status_string", "gb_last_error"]
+            "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel"]
 
 
 def library_path() -> str:
@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
         L.gb_solve_adjoint.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_dnu.argtypes = [vp, vp, vp, i32, vp]
         L.gb_apply.argtypes = [vp, i32, vp, vp]
+        L.gb_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
         L.gb_export.argtypes = [vp, i32, vp, vp, vp]
         L.gb_destroy.argtypes = [vp]
         L.gb_destroy.restype = None
@@ -237,6 +238,16 @@ class Stokes:
         out = np.zeros(k)
         _check(load_library().gb_dnu(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
         return out
+
+    KERNELS = {"cg_spmv": 0, "ic0_apply": 1, "stokes_apply": 2, "trsv_fwd": 3}
+
+    def time_kernel(self, which, reps=20):
+        """Mean ms per launch of one kernel family of the last solve (events
+        on the library's stream): 'cg_spmv', 'ic0_apply', 'stokes_apply',
+        'trsv_fwd'."""
+        ms = C.c_double(0.0)
+        _check(load_library().gb_time_kernel(self._h, self.KERNELS[which], int(reps), C.byref(ms)))
+        return ms.value
 
     def apply(self, which, x):
         """which: 'K' (Stokes operator), 'A', 'B', 'Bt' -- natural numbering."""

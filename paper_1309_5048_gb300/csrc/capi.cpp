@@ -232,6 +232,14 @@ int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double*
   });
 }
 
+int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
+  if (!h || !ms_host) return GB_ERR_INVALID_ARG;
+  return guarded([&] {
+    StreamOrder order(h->c);
+    *ms_host = time_kernel(h->c, which, reps);
+  });
+}
+
 int gb_apply(gb_ctx* h, int which, const double* x_dev, double* y_dev) {
   if (!h) return GB_ERR_INVALID_ARG;
   return guarded([&] {

@@ -7,8 +7,7 @@
 
 namespace gbs {
 
-constexpr int kBlock = 256;        // threads per block for vector kernels
-constexpr int kRedBlocksMax = 1216;  // 152 SMs x 8: upper bound on reduction grids
+constexpr int kBlock = 256;  // threads per block for vector kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -98,22 +97,21 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 }
 
 // Inside the last block: total[slot*NS+s] = sum over blocks of partials, in
-// a fixed order (strided per thread, then a fixed shared-memory tree).
+// a fixed order.  Each of the K*NS sums gets TPS consecutive threads (a
+// power of two <= 32); each thread adds a fixed strided subset of the blocks,
+// then the TPS threads combine with a fixed shuffle tree.
 template <int K, int NS>
 __device__ __forceinline__ void finalize_partials(const double* partial, int nblocks, double* total) {
-  __shared__ double red[kBlock];
-  for (int idx = 0; idx < K * NS; ++idx) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partial[(size_t)b * K * NS + idx];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) total[idx] = red[0];
-    __syncthreads();
-  }
+  constexpr int NSUM = K * NS;
+  constexpr int TPS = (kBlock / NSUM >= 32) ? 32 : (kBlock / NSUM >= 16 ? 16 : (kBlock / NSUM >= 8 ? 8 : (kBlock / NSUM >= 4 ? 4 : (kBlock / NSUM >= 2 ? 2 : 1))));
+  static_assert(NSUM * TPS <= kBlock, "too many sums for one block");
+  const int idx = threadIdx.x / TPS, sub = threadIdx.x % TPS;
+  double acc = 0.0;
+  if (idx < NSUM)
+    for (int b = sub; b < nblocks; b += TPS) acc += partial[(size_t)b * NSUM + idx];
+  acc = group_sum<TPS>(acc);
+  if (sub == 0 && idx < NSUM) total[idx] = acc;
+  __syncthreads();
 }
 
 // Knot xi_j of the uniform open knot vector of degree q with N elements.

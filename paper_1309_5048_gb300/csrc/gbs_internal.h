@@ -53,13 +53,6 @@ struct DevBuf {
   void zero(cudaStream_t s);
 };
 
-// Reduction buffer: per-block partials and a completion counter; the last
-// block to finish reduces the partials in a fixed order (deterministic).
-struct RedBuf {
-  double* partial = nullptr;  // [maxblocks][K][nsums]
-  unsigned* counter = nullptr;
-};
-
 // Per-RHS scalar state of the solver, structure of arrays [field][K].
 enum ScalarField {
   // MINRES
@@ -74,7 +67,8 @@ enum ScalarField {
 
 struct Workspace {
   int K = 0;          // padded batch width
-  int k = 0;          // live right-hand sides
+  int k = 0;          // capacity (right-hand sides) of the staging buffers
+  int last_k = 0;     // right-hand sides of the most recent solve (0: none)
   int precision = -1;
   size_t n = 0;       // n_u + n_p
   // MINRES (FP64): x, three Lanczos vectors, two z buffers, three w buffers, q
@@ -91,7 +85,6 @@ struct Workspace {
   void* cg_y = nullptr;
   void* cg_p = nullptr;
   void* cg_q = nullptr;
-  void* cg_b = nullptr;
   double* S = nullptr;          // scalars [S_NFIELDS][K]
   double* S_host = nullptr;     // pinned mirror
   int* flag = nullptr;          // device: [0] any outer active, [1] any inner active
@@ -167,6 +160,7 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
 int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_solve_opts& o,
                gb_info* info);
 void apply_operator(Ctx& c, int which, const double* x, double* y);
+double time_kernel(Ctx& c, int which, int reps);
 void dnu(Ctx& c, const double* lam, const double* x, int k, double* out);
 void release_workspace(Ctx& c);
 

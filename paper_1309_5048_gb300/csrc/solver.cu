@@ -160,19 +160,29 @@ struct Run {
   void stokes() { k_stokes_apply<K><<<grid_cap(n() * G), kBlock, 0, s>>>(a); }
   void gamma() { k_gamma<K, T><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
   void update() { k_update<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
+  // One kernel per level, launched with programmatic dependent launch so a
+  // level's independent loads overlap the previous level (k_trsv_level).
+  template <bool FWD>
+  void level(int l) {
+    const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
+    const int64_t th = (int64_t)(r1 - r0) * G;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((th + kBlock - 1) / kBlock));
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
+  }
   void trsv_fwd() {
-    for (int l = 0; l < c.nlev; ++l) {
-      const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
-      const int64_t th = (int64_t)(r1 - r0) * G;
-      k_trsv_level<K, T, true><<<(unsigned)((th + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r0, r1);
-    }
+    for (int l = 0; l < c.nlev; ++l) level<true>(l);
   }
   void trsv_bwd() {
-    for (int l = c.nlev - 1; l >= 0; --l) {
-      const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
-      const int64_t th = (int64_t)(r1 - r0) * G;
-      k_trsv_level<K, T, false><<<(unsigned)((th + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r0, r1);
-    }
+    for (int l = c.nlev - 1; l >= 0; --l) level<false>(l);
   }
   void cg_prologue() {
     trsv_fwd();
@@ -336,15 +346,77 @@ int collect_info(Ctx& c, int k, gb_info* info) {
     I.relres_est = f(S_RELRES);
     I.relres_true = f(S_TRUE_RES);
     int st = GB_OK;
-    if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
+    if (f(S_STATUS) == 3.0) st = GB_ERR_DEVICE_TIMEOUT;
+    else if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
     else if (f(S_STATUS) != 0.0) st = GB_ERR_NOT_CONVERGED;
     I.status = st;
-    if (st == GB_ERR_NONFINITE || (st != GB_OK && worst == GB_OK)) worst = st;
+    if (st == GB_ERR_DEVICE_TIMEOUT || (st == GB_ERR_NONFINITE && worst != GB_ERR_DEVICE_TIMEOUT) ||
+        (st != GB_OK && worst == GB_OK))
+      worst = st;
   }
   return worst;
 }
 
+// Timing of one kernel family with the last solve's configuration.
+template <int K, class T>
+double time_family(Ctx& c, int which, int reps) {
+  Workspace& w = c.ws;
+  Args a = make_args(c, nullptr, w.last_k);
+  Run<K, T> run(c, a);
+  std::vector<double> saved(S_NFIELDS * K), act;
+  GBS_CUDA(cudaMemcpyAsync(saved.data(), w.S, sizeof(double) * saved.size(), cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  act = saved;
+  for (int t = 0; t < w.last_k; ++t) {
+    act[S_CG_ACTIVE * K + t] = 1.0;
+    act[S_OUTER_ACTIVE * K + t] = 1.0;
+    if (act[S_GAMMA * K + t] == 0.0) act[S_GAMMA * K + t] = 1.0;
+    if (act[S_RHO * K + t] == 0.0) act[S_RHO * K + t] = 1.0;
+  }
+  GBS_CUDA(cudaMemcpyAsync(w.S, act.data(), sizeof(double) * act.size(), cudaMemcpyHostToDevice, c.stream));
+  auto launch = [&] {
+    switch (which) {
+      case 0: k_cg_spmv<K, T><<<grid_cap(c.n_u * Map<K>::G), kBlock, 0, c.stream>>>(run.a); break;
+      case 1: run.trsv_fwd(); run.trsv_bwd(); break;
+      case 2: run.stokes(); break;
+      default: run.trsv_fwd(); break;
+    }
+  };
+  launch();
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) GBS_CUDA(cudaEventCreate(&e));
+  for (int r = 0; r < reps; ++r) {
+    GBS_CUDA(cudaEventRecord(ev[2 * r], c.stream));
+    launch();
+    GBS_CUDA(cudaEventRecord(ev[2 * r + 1], c.stream));
+  }
+  GBS_CUDA(cudaEventSynchronize(ev.back()));
+  double ms = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    float m = 0.f;
+    GBS_CUDA(cudaEventElapsedTime(&m, ev[2 * r], ev[2 * r + 1]));
+    ms += m;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  GBS_CUDA(cudaGetLastError());
+  GBS_CUDA(cudaMemcpyAsync(w.S, saved.data(), sizeof(double) * saved.size(), cudaMemcpyHostToDevice, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  return ms / reps;
+}
+
 }  // namespace
+
+double time_kernel(Ctx& c, int which, int reps) {
+  Workspace& w = c.ws;
+  if (w.last_k < 1 || !w.x) fail(GB_ERR_INVALID_ARG, "time_kernel needs a completed solve");
+  if (which < 0 || which > 3 || reps < 1 || reps > 100000) fail(GB_ERR_INVALID_ARG, "bad time_kernel request");
+  const bool mixed = w.precision == GB_PREC_MIXED;
+  switch (w.K) {
+    case 1: return mixed ? time_family<1, float>(c, which, reps) : time_family<1, double>(c, which, reps);
+    case 8: return mixed ? time_family<8, float>(c, which, reps) : time_family<8, double>(c, which, reps);
+    default: return mixed ? time_family<32, float>(c, which, reps) : time_family<32, double>(c, which, reps);
+  }
+}
 
 void release_workspace(Ctx& c) {
   Workspace& w = c.ws;
@@ -403,6 +475,7 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
       break;
   }
   GBS_CUDA(cudaGetLastError());
+  w.last_k = k;
   return collect_info(c, k, info);
 }
 

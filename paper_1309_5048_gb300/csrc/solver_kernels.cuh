@@ -26,7 +26,7 @@ namespace gbs {
 
 namespace {
 
-constexpr int kRB = 304;  // blocks of the reduction kernels (2 per SM)
+constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
 
 struct Args {
   int n_u, n_p, k;
@@ -520,37 +520,64 @@ __global__ void k_cg_axpy(Args a) {
   }
 }
 
-// One level of a triangular solve, rows [r0, r1) of the internal numbering:
+// One level of a triangular solve, internal rows [r0, r1):
 //   forward  (L):   y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii
 //   backward (L^T): z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii
 // The rows of a level depend only on rows of earlier (forward) or later
-// (backward) levels, which earlier launches have finished.
+// (backward) levels.  Levels are launched back to back with programmatic
+// dependent launch: each level kernel lets the next one start at once; the
+// next one loads what does not depend on earlier kernels (row pointers,
+// column indices, factor values, 1/L_ii) and then waits for its predecessor
+// grid (cudaGridDependencySynchronize) before it reads the right-hand side,
+// the CG state and the solution entries it depends on.  A level then costs
+// about one memory round trip for those entries plus its stores, instead of
+// a launch and three dependent round trips.
 template <int K, class T, bool FWD>
-__global__ void k_trsv_level(Args a, int r0, int r1) {
+__global__ void __launch_bounds__(kBlock) k_trsv_level(Args a, int r0, int r1) {
   using M = Map<K>;
+  constexpr int PF = 6;  // entries per lane fetched before the wait
+  constexpr int STEP = (K == 1) ? M::G : 1;
+  cudaTriggerProgrammaticLaunchCompletion();
   const int32_t* __restrict__ ptr = FWD ? a.L_ptr : a.U_ptr;
   const int32_t* __restrict__ col = FWD ? a.L_col : a.U_col;
   const T* __restrict__ val = FWD ? pick<T>(a.L_val, a.L_val32) : pick<T>(a.U_val, a.U_val32);
   const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
-  const T* __restrict__ rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
-  T* __restrict__ out = (T*)(FWD ? a.cg_y : a.cg_z);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
   const int lane = threadIdx.x & 31;
   const int g = lane % M::G;
   const int t = (K == 1) ? 0 : g;
-  if (SF(a, S_CG_ACTIVE, t, K) == 0.0) return;  // uniform per group of lanes
-  const int row = r0 + (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
-  if (row >= r1) return;
+  const int row = r0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) / M::G);
+  const bool act = row < r1;  // uniform over a lane group
+  int eb = 0, ee = 0;
+  int cc[PF];
+  T v[PF];
+  T ii = T(0);
+  if (act) {
+    eb = ptr[row] + ((K == 1) ? g : 0);
+    ee = ptr[row + 1];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int e = eb + u * STEP;
+      cc[u] = e < ee ? col[e] : 0;
+      v[u] = e < ee ? val[e] : T(0);
+    }
+    ii = inv[row];
+  }
+  cudaGridDependencySynchronize();
+  if (!act || SF(a, S_CG_ACTIVE, t, K) == 0.0) return;  // uniform over a lane group
   T s = 0;
+#pragma unroll
+  for (int u = 0; u < PF; ++u)
+    if (eb + u * STEP < ee) s += v[u] * __ldcg(out + ((K == 1) ? (size_t)cc[u] : (size_t)cc[u] * K + t));
+  for (int e = eb + PF * STEP; e < ee; e += STEP)
+    s += val[e] * __ldcg(out + ((K == 1) ? (size_t)col[e] : (size_t)col[e] * K + t));
   if (K == 1) {
-    for (int e = ptr[row] + g; e < ptr[row + 1]; e += M::G) s += val[e] * out[col[e]];
     if (sizeof(T) == 8) s = (T)group_sum<M::G>((double)s);
     else s = (T)group_sumf<M::G>((float)s);
-    if (g == 0) out[row] = (rhs[row] - s) * inv[row];
-  } else {
-    for (int e = ptr[row]; e < ptr[row + 1]; ++e) s += val[e] * out[(size_t)col[e] * K + t];
-    const size_t idx = (size_t)row * K + t;
-    out[idx] = (rhs[idx] - s) * inv[row];
   }
+  const size_t ridx = (K == 1) ? (size_t)row : (size_t)row * K + t;
+  if (K > 1 || g == 0) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
 }
 
 // rho = r^T z.  init: p = z, rho.  Otherwise beta = rho_new / rho.

@@ -273,12 +273,13 @@ def test_edge_cases(oracle_mod, gb):
     _, rhs = _rhs(ref, s, "fourier", seed=1)
     x, info = s.solve(rhs, tol=1e-14, max_outer=3)
     assert info["status"] == 5 and info["outer_its"] == 3 and torch.isfinite(x).all()
-    # indefinite A (negative Nitsche constant): IC(0) breakdown at the oracle's row
-    refb = oracle_mod.Problem(2, 6, 3, cpen=-40.0)
+    # C_pen too small for coercivity (Sec. 4): A_h indefinite, IC(0) breaks
+    # down, at the oracle's row (C_pen = 1 fails at a later row than the first)
+    refb = oracle_mod.Problem(2, 6, 3, cpen=1.0)
     row_ref = refb.factor()
-    assert row_ref >= 0
+    assert row_ref > 0
     sb = gb.Stokes(2, 6, 3)
-    sb.assemble(1.0, -40.0)
+    sb.assemble(1.0, 1.0)
     with pytest.raises(gb.GbError) as ei:
         sb.factor_ic0()
     assert ei.value.row == row_ref
