@@ -412,6 +412,7 @@ def main():
             "inner_its_mean": infos[0]["inner_its_total"] / max(infos[0]["precond_apps"], 1),
             "relres_est": infos[0]["relres_est"], "relres_true": infos[0]["relres_true"],
             "setup_s": t_setup, "assemble_factor_s": t_rf, "levels": s.nlevels,
+            "layouts": dict(zip(("spmv", "trsv"), s.kernel_variants(args.precision))),
             "kernels": kern, "variants": variants,
         }
         print(json.dumps(line), flush=True)

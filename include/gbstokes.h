@@ -174,6 +174,15 @@ int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, doubl
  * x_dev / y_dev sizes follow the operator. */
 int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
+/* Kernel layout of single-right-hand-side solves (k == 1) for one precision
+ * (GB_PREC_*): spmv / trsv = 0 CSR with 8 lanes per row, 1 SELL-32 with one
+ * thread per row, -1 automatic.  Automatic (the default) times both layouts
+ * on this problem at the first single-RHS solve of that precision and keeps
+ * the faster one; the layouts differ only in the summation order inside a
+ * row.  gb_get_kernel_variants reports the current choice (-1: not made). */
+int gb_set_kernel_variants(gb_ctx* ctx, int precision, int spmv, int trsv);
+int gb_get_kernel_variants(const gb_ctx* ctx, int precision, int* spmv, int* trsv);
+
 /* Benchmark instrumentation.  Times `reps` (>= 1) launches of one kernel
  * family of the most recent gb_solve, with the same batch width, precision
  * and launch configuration, on the context's stream with CUDA events, after

@@ -53,7 +53,8 @@ class gb_info(C.Structure):
 
 EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
-            "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel"]
+            "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel",
+            "gb_set_kernel_variants", "gb_get_kernel_variants"]
 
 
 def library_path() -> str:
@@ -87,6 +88,8 @@ def load_library(build_if_missing: bool = True):
         L.gb_dnu.argtypes = [vp, vp, vp, i32, vp]
         L.gb_apply.argtypes = [vp, i32, vp, vp]
         L.gb_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
+        L.gb_set_kernel_variants.argtypes = [vp, i32, i32, i32]
+        L.gb_get_kernel_variants.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.gb_export.argtypes = [vp, i32, vp, vp, vp]
         L.gb_destroy.argtypes = [vp]
         L.gb_destroy.restype = None
@@ -238,6 +241,20 @@ class Stokes:
         out = np.zeros(k)
         _check(load_library().gb_dnu(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
         return out
+
+    LAYOUTS = {"auto": -1, "csr": 0, "sell": 1}
+
+    def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
+        """Layout of the single-RHS inner SpMV and IC(0) sweeps: 'csr' (8
+        lanes per row), 'sell' (SELL-32, one thread per row) or 'auto'."""
+        _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.LAYOUTS[spmv],
+                                                      self.LAYOUTS[trsv]))
+
+    def kernel_variants(self, precision="fp64"):
+        a, b = C.c_int(0), C.c_int(0)
+        _check(load_library().gb_get_kernel_variants(self._h, PRECISIONS[precision], C.byref(a), C.byref(b)))
+        names = {-1: "unset", 0: "csr", 1: "sell"}
+        return names[a.value], names[b.value]
 
     KERNELS = {"cg_spmv": 0, "ic0_apply": 1, "stokes_apply": 2, "trsv_fwd": 3}
 

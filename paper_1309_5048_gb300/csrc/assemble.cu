@@ -498,6 +498,7 @@ void assemble(Ctx& c, double nu, double cpen) {
   GBS_CUDA(cudaGetLastError());
   k_gather_bt<<<grid_for(c.nnzB, 256), 256, 0, c.stream>>>((int)c.nnzB, c.Bt_map.p, c.B_val.p, c.Bt_val.p);
   GBS_CUDA(cudaGetLastError());
+  sell_refill(c, c.sA, c.A_val.p);
   k_pressure_diag<<<grid_for(c.n_p, 256), 256, 0, c.stream>>>(P, (int)c.n_p, c.Qdiag.p, c.wmean.p);
   GBS_CUDA(cudaGetLastError());
   GBS_CUDA(cudaStreamSynchronize(c.stream));

@@ -232,6 +232,27 @@ int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double*
   });
 }
 
+int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
+  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 1 || trsv < -1 || trsv > 1) {
+    set_error("bad kernel variant request");
+    return GB_ERR_INVALID_ARG;
+  }
+  h->c.var_spmv[precision] = spmv;
+  h->c.var_trsv[precision] = trsv;
+  h->c.ws.graph_valid = false;
+  return GB_OK;
+}
+
+int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv) {
+  if (!h || precision < 0 || precision > 1 || !spmv || !trsv) {
+    set_error("bad kernel variant query");
+    return GB_ERR_INVALID_ARG;
+  }
+  *spmv = h->c.var_spmv[precision];
+  *trsv = h->c.var_trsv[precision];
+  return GB_OK;
+}
+
 int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
   if (!h || !ms_host) return GB_ERR_INVALID_ARG;
   return guarded([&] {

@@ -79,7 +79,23 @@ __global__ void k_factor_finish(int n, int nnzL, int nnzU, const double* __restr
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) L_inv32[t] = (float)L_inv[t];
 }
 
+__global__ void k_sell_fill(int64_t slots, const int32_t* __restrict__ src, const double* __restrict__ csr,
+                            double* __restrict__ val, float* __restrict__ val32) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < slots; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = src[t];
+    const double v = k >= 0 ? csr[k] : 0.0;
+    val[t] = v;
+    val32[t] = (float)v;
+  }
+}
+
 }  // namespace
+
+void sell_refill(Ctx& c, Sell& S, const double* csr_val) {
+  if (S.slots == 0) return;
+  k_sell_fill<<<152 * 8, 256, 0, c.stream>>>(S.slots, S.src.p, csr_val, S.val.p, S.val32.p);
+  GBS_CUDA(cudaGetLastError());
+}
 
 int64_t factor_ic0(Ctx& c) {
   if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble before factor_ic0");
@@ -100,6 +116,8 @@ int64_t factor_ic0(Ctx& c) {
   k_factor_finish<<<152 * 8, 256, 0, c.stream>>>(n, nnzL, nnzU, c.L_val.p, c.L_inv.p, c.U_map.p,
                                                  c.U_val.p, c.L_val32.p, c.U_val32.p, c.L_inv32.p);
   GBS_CUDA(cudaGetLastError());
+  sell_refill(c, c.sL, c.L_val.p);
+  sell_refill(c, c.sU, c.U_val.p);
   int bad = 0;
   GBS_CUDA(cudaMemcpyAsync(&bad, c.status_d.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));

@@ -65,6 +65,20 @@ enum ScalarField {
   S_NFIELDS
 };
 
+// SELL-32 copy of a CSR matrix (single right-hand-side kernels, one thread per
+// row): rows are cut into slices of 32 consecutive rows that never cross a
+// level of the IC(0) DAG; entry k of the row in lane i of slice s sits at
+// off[s] + 32 k + i.  rowlen[row] bounds each row (padding is never read);
+// src maps every slot to the position of its value in the CSR value array
+// (-1 for padding), so values are refilled after assembly / factorisation.
+struct Sell {
+  DevBuf<int32_t> off, row0, rowlen, col, src;
+  DevBuf<double> val;
+  DevBuf<float> val32;
+  int64_t slots = 0;
+  int nslices = 0;
+};
+
 struct Workspace {
   int K = 0;          // padded batch width
   int k = 0;          // capacity (right-hand sides) of the staging buffers
@@ -139,6 +153,12 @@ struct Ctx {
   DevBuf<double> B_val, Bt_val;
   DevBuf<double> Qdiag, wmean;
   DevBuf<double> tab1d;  // 1D integral tables (assembly)
+  Sell sA, sL, sU;                 // SELL-32 copies of A, L, U
+  std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
+  // kernel layout per precision (index 0 FP64, 1 mixed) for single-RHS
+  // solves: 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row, -1 not
+  // chosen yet (timed at the first single-RHS solve)
+  int var_spmv[2] = {-1, -1}, var_trsv[2] = {-1, -1};
   DevBuf<int> status_d;  // device error flags
   double nu = 1.0, cpen = 0.0;
   bool assembled = false, factored = false;
@@ -154,6 +174,7 @@ void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, d
 void load_manufactured(Ctx& c, double* f_dev);
 // factor.cu
 int64_t factor_ic0(Ctx& c);
+void sell_refill(Ctx& c, Sell& S, const double* csr_val);
 // solver.cu
 int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts& o,
           gb_info* info, bool adjoint);

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "solver_kernels.cuh"
@@ -130,6 +131,20 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.jcur = w.flag + 2;
   a.partial = w.partial;
   a.counter = w.counter;
+  auto view = [](const Sell& S) {
+    SellView v;
+    v.off = S.off.p;
+    v.row0 = S.row0.p;
+    v.rowlen = S.rowlen.p;
+    v.col = S.col.p;
+    v.val = S.val.p;
+    v.val32 = S.val32.p;
+    v.nslices = S.nslices;
+    return v;
+  };
+  a.sA = view(c.sA);
+  a.sL = view(c.sL);
+  a.sU = view(c.sU);
   if (o) {
     a.tol = o->tol;
     a.inner_tol = o->inner_tol;
@@ -151,8 +166,13 @@ struct Run {
   Ctx& c;
   Args a;
   cudaStream_t s;
+  int vspmv = 0, vtrsv = 0;  // single-RHS layout: 0 CSR (8 lanes per row), 1 SELL-32
   static constexpr int G = Map<K>::G;
-  Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {}
+  Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    vspmv = K == 1 ? std::max(0, c.var_spmv[pi]) : 0;
+    vtrsv = K == 1 ? std::max(0, c.var_trsv[pi]) : 0;
+  }
   int64_t n() const { return c.n_u + c.n_p; }
 
   void gather(const double* rhs) { k_gather<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a, rhs); }
@@ -164,8 +184,10 @@ struct Run {
   // level's independent loads overlap the previous level (k_trsv_level).
   template <bool FWD>
   void level(int l) {
-    const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
-    const int64_t th = (int64_t)(r1 - r0) * G;
+    const bool sell = (K == 1 && vtrsv == 1);
+    const int r0 = sell ? c.lev_slice[l] : c.lev_ptr[l];
+    const int r1 = sell ? c.lev_slice[l + 1] : c.lev_ptr[l + 1];
+    const int64_t th = (int64_t)(r1 - r0) * (sell ? 32 : G);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((th + kBlock - 1) / kBlock));
     cfg.blockDim = dim3(kBlock);
@@ -176,7 +198,12 @@ struct Run {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
+    if (sell) GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sell<T, FWD>, a, r0, r1));
+    else GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
+  }
+  void spmv() {
+    if (K == 1 && vspmv == 1) k_cg_spmv_sell<T><<<grid_cap((int64_t)c.sA.nslices * 32), kBlock, 0, s>>>(a);
+    else k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
   }
   void trsv_fwd() {
     for (int l = 0; l < c.nlev; ++l) level<true>(l);
@@ -190,7 +217,7 @@ struct Run {
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 1);
   }
   void cg_head() {
-    k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
+    spmv();
     k_cg_axpy<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
   void cg_tail() {
@@ -306,8 +333,56 @@ struct Run {
   }
 };
 
+// Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
+// SELL-32 (thread per row) forms of the inner SpMV and of one IC(0)
+// application on this problem and keep the faster; SELL must win by 3% to
+// replace CSR.  Runs once per precision, outside any graph capture; the
+// choice only changes the summation order inside a row.
+template <class T>
+void autotune_single(Ctx& c) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  if (c.var_spmv[pi] >= 0 && c.var_trsv[pi] >= 0) return;
+  Workspace& w = c.ws;
+  k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_p, c.n_u, T(1));
+  k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_r, c.n_u, T(1));
+  const double live[2] = {1.0, 1.0};
+  GBS_CUDA(cudaMemcpyAsync(w.S + S_CG_ACTIVE, &live[0], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  GBS_CUDA(cudaMemcpyAsync(w.S + S_RHO, &live[1], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  Args a = make_args(c, nullptr, 1);
+  cudaEvent_t e0, e1;
+  GBS_CUDA(cudaEventCreate(&e0));
+  GBS_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](int variant, int which) {
+    Run<1, T> run(c, a);
+    run.vspmv = variant;
+    run.vtrsv = variant;
+    const int reps = which == 0 ? 20 : 5;
+    auto launch = [&] {
+      if (which == 0) run.spmv();
+      else {
+        run.trsv_fwd();
+        run.trsv_bwd();
+      }
+    };
+    launch();
+    GBS_CUDA(cudaEventRecord(e0, c.stream));
+    for (int r = 0; r < reps; ++r) launch();
+    GBS_CUDA(cudaEventRecord(e1, c.stream));
+    GBS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  if (c.var_spmv[pi] < 0) c.var_spmv[pi] = time_it(1, 0) < 0.97f * time_it(0, 0) ? 1 : 0;
+  if (c.var_trsv[pi] < 0) c.var_trsv[pi] = time_it(1, 1) < 0.97f * time_it(0, 1) ? 1 : 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GBS_CUDA(cudaGetLastError());
+}
+
 template <int K, class T>
 void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solve_opts& o) {
+  if (K == 1) autotune_single<T>(c);
   Args a = make_args(c, &o, k);
   Run<K, T> run(c, a);
   Workspace& w = c.ws;
@@ -317,7 +392,7 @@ void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solv
   }
   std::vector<double> key = {(double)(uintptr_t)rhs, (double)(uintptr_t)out, (double)k, o.tol, o.inner_tol,
                              (double)o.max_outer, (double)o.max_inner, (double)K, (double)o.precision,
-                             (double)a.nforced, c.nu};
+                             (double)a.nforced, c.nu, (double)run.vspmv, (double)run.vtrsv};
   if (!w.graph_valid || w.graph_key != key) {
     if (w.graph) {
       cudaGraphExecDestroy(w.graph);
@@ -376,7 +451,7 @@ double time_family(Ctx& c, int which, int reps) {
   GBS_CUDA(cudaMemcpyAsync(w.S, act.data(), sizeof(double) * act.size(), cudaMemcpyHostToDevice, c.stream));
   auto launch = [&] {
     switch (which) {
-      case 0: k_cg_spmv<K, T><<<grid_cap(c.n_u * Map<K>::G), kBlock, 0, c.stream>>>(run.a); break;
+      case 0: run.spmv(); break;
       case 1: run.trsv_fwd(); run.trsv_bwd(); break;
       case 2: run.stokes(); break;
       default: run.trsv_fwd(); break;

@@ -28,6 +28,14 @@ namespace {
 
 constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
 
+// Device view of a SELL-32 matrix copy (see Sell in gbs_internal.h).
+struct SellView {
+  const int32_t *off, *row0, *rowlen, *col;
+  const double* val;
+  const float* val32;
+  int nslices;
+};
+
 struct Args {
   int n_u, n_p, k;
   // matrices (internal numbering)
@@ -59,6 +67,7 @@ struct Args {
   unsigned* counter;
   cudaGraphConditionalHandle h_outer, h_inner;
   int use_handles;
+  SellView sA, sL, sU;  // SELL-32 copies used by the single-RHS variants
 };
 
 template <int K>
@@ -578,6 +587,94 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level(Args a, int r0, int r1) {
   }
   const size_t ridx = (K == 1) ? (size_t)row : (size_t)row * K + t;
   if (K > 1 || g == 0) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
+}
+
+// ---- SELL-32 variants (single right-hand side, one thread per row) --------
+// The 32 lanes of a warp read 32 consecutive slots, so every load of values
+// and column indices is coalesced and no cross-lane reduction is needed (on
+// GB300 the shuffle-tree DADDs of the 8-lane CSR form cost as much FP64 issue
+// as the useful FMAs).  Each row sums its entries in order.
+
+// q = A p and p^T q; epilogue alpha = rho / p^T q (as k_cg_spmv).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_cg_spmv_sell(Args a) {
+  const SellView m = a.sA;
+  const T* __restrict__ val = pick<T>(m.val, m.val32);
+  const T* __restrict__ p = (const T*)a.cg_p;
+  T* __restrict__ q = (T*)a.cg_q;
+  double vals[1] = {0.0};
+  if (SF(a, S_CG_ACTIVE, 0, 1) != 0.0) {
+    const int total = m.nslices * 32;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+      const int s = i >> 5, lane = i & 31;
+      const int row = m.row0[s] + lane;
+      if (row >= m.row0[s + 1]) continue;
+      const int base = m.off[s] + lane, len = m.rowlen[row];
+      T y = 0;
+      for (int k = 0; k < len; ++k) y += val[base + 32 * k] * p[m.col[base + 32 * k]];
+      q[row] = y;
+      vals[0] += (double)y * (double)p[row];
+    }
+  }
+  block_partials<1, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[1];
+    finalize_partials<1, 1>(a.partial, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      if (SF(a, S_CG_ACTIVE, 0, 1) != 0.0) SF(a, S_ALPHA, 0, 1) = SF(a, S_RHO, 0, 1) / tot[0];
+      *a.counter = 0;
+    }
+  }
+}
+
+// One level of a triangular solve over the slices [s0, s1) of that level
+// (same recurrences and the same programmatic-dependent-launch structure as
+// k_trsv_level).
+template <class T, bool FWD>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int s1) {
+  constexpr int PF = 8;  // entries per row fetched before the wait
+  cudaTriggerProgrammaticLaunchCompletion();
+  const SellView m = FWD ? a.sL : a.sU;
+  const T* __restrict__ val = pick<T>(m.val, m.val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + (i >> 5), lane = i & 31;
+  int row = 0, base = 0, len = 0;
+  bool act = s < s1;
+  if (act) {
+    row = m.row0[s] + lane;
+    act = row < m.row0[s + 1];
+  }
+  int cc[PF];
+  T v[PF];
+  T ii = T(0);
+  if (act) {
+    base = m.off[s] + lane;
+    len = m.rowlen[row];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      cc[k] = k < len ? m.col[base + 32 * k] : 0;
+      v[k] = k < len ? val[base + 32 * k] : T(0);
+    }
+    ii = inv[row];
+  }
+  cudaGridDependencySynchronize();
+  if (!act || SF(a, S_CG_ACTIVE, 0, 1) == 0.0) return;
+  T sum = 0;
+#pragma unroll
+  for (int k = 0; k < PF; ++k)
+    if (k < len) sum += v[k] * __ldcg(out + cc[k]);
+  for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
+  out[row] = (__ldcg(rhs + row) - sum) * ii;
+}
+
+// x[i] = v (kernel timing and layout tuning only).
+template <class T>
+__global__ void k_fill_value(T* __restrict__ x, int64_t n, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
 }
 
 // rho = r^T z.  init: p = z, rho.  Otherwise beta = rho_new / rho.

@@ -290,6 +290,35 @@ def test_edge_cases(oracle_mod, gb):
         gb.Stokes(4, 3, 3)
 
 
+@pytest.mark.parametrize("spmv,trsv", [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr")])
+@pytest.mark.parametrize("dim,N,p", [(2, 13, 3), (3, 3, 3)])
+def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p):
+    """Both single-RHS layouts (CSR 8 lanes per row, SELL-32 thread per row)
+    of the inner SpMV and the IC(0) sweeps reproduce the oracle (<= 1e-10)."""
+    ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
+    assert ref.factor() < 0
+    s.factor_ic0()
+    s.set_kernel_variants("fp64", spmv, trsv)
+    s.set_kernel_variants("mixed", spmv, trsv)
+    assert s.kernel_variants("fp64") == (spmv, trsv)
+    b, rhs = _rhs(ref, s, "fourier", seed=11)
+    xr, ir = ref.minres(b, tol=1e-8, inner_tol=1e-2)
+    x, info = s.solve(rhs, tol=1e-8, inner_tol=1e-2, forced=ir["counts"])
+    assert rel(x.cpu().numpy(), xr) <= 1e-10
+    x10, _ = s.solve(rhs, tol=1e-10, inner_tol=1e-2, precision="mixed")
+    xr10, _ = ref.minres(b, tol=1e-10, inner_tol=1e-2)
+    assert rel(x10.cpu().numpy(), xr10) <= 1e-7
+
+
+def test_layout_autotune_makes_a_choice(oracle_mod, gb):
+    _, s = make_pair(oracle_mod, gb, 2, 20, 3, "multicolour")
+    s.factor_ic0()
+    assert s.kernel_variants("fp64") == ("unset", "unset")
+    _, rhs = _rhs(oracle_mod.Problem(2, 20, 3), s, "fourier", seed=3)
+    s.solve(rhs, tol=1e-6)
+    assert all(v in ("csr", "sell") for v in s.kernel_variants("fp64"))
+
+
 @pytest.mark.slow
 def test_full_size_2d_256_replay_parity(oracle_mod, gb):
     """The benchmark workload (2D, 256 x 256 elements, k' = 2, Fourier
