@@ -169,6 +169,21 @@ int gb_solve_adjoint(gb_ctx* ctx, const double* grad_dev, double* lam_dev, int k
  * lam_dev, x_dev: [k][n_u + n_p]; out_host: k doubles. */
 int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
 
+/* The same dL/dnu as gb_dnu, computed without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code running while a CUDA graph is being
+ * captured, programs whose device memory belongs to a pool or framework that
+ * forbids further allocations, callers with an exhausted memory budget.
+ * (gb_dnu may allocate the context's workspace on first use.)  The reduction
+ * scratch is a static device array inside the library, sized for k <= 32 and
+ * the largest launch (about 304 KiB); every GPU that loads the library holds
+ * it until the process exits.  k > 32 is rejected with GB_ERR_INVALID_ARG.
+ * The first call on a device looks up that array's device address (make it
+ * before any stream capture).  All calls share the array, so calls that
+ * overlap on the GPU race; the context must be assembled.  Arguments, layout
+ * and result are those of gb_dnu. */
+int gb_dnu_noalloc(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
+
 /* y = K x (which = 0), y_u = A_h x_u (which = 1), y_p = B x_u (which = 2),
  * y_u = B^T x_p (which = 3), all in natural numbering, FP64, one vector.
  * x_dev / y_dev sizes follow the operator. */

@@ -54,7 +54,7 @@ class gb_info(C.Structure):
 EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
             "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel",
-            "gb_set_kernel_variants", "gb_get_kernel_variants"]
+            "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc"]
 
 
 def library_path() -> str:
@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
         L.gb_solve_host.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_solve_adjoint.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_dnu.argtypes = [vp, vp, vp, i32, vp]
+        L.gb_dnu_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.gb_apply.argtypes = [vp, i32, vp, vp]
         L.gb_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
         L.gb_set_kernel_variants.argtypes = [vp, i32, i32, i32]
@@ -265,6 +266,16 @@ class Stokes:
         ms = C.c_double(0.0)
         _check(load_library().gb_time_kernel(self._h, self.KERNELS[which], int(reps), C.byref(ms)))
         return ms.value
+
+    def dnu_noalloc(self, lam, x):
+        """gb_dnu_noalloc: dL/dnu like dnu(), with no device allocation (for
+        callers that cannot allocate; see include/gbstokes.h)."""
+        lam = self._dev(lam).reshape(-1, self.n)
+        x = self._dev(x).reshape(-1, self.n)
+        k = lam.shape[0]
+        out = np.zeros(k)
+        _check(load_library().gb_dnu_noalloc(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def apply(self, which, x):
         """which: 'K' (Stokes operator), 'A', 'B', 'Bt' -- natural numbering."""

@@ -261,6 +261,14 @@ int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
   });
 }
 
+int gb_dnu_noalloc(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double* out_host) {
+  if (!h) return GB_ERR_INVALID_ARG;
+  return guarded([&] {
+    StreamOrder order(h->c);
+    dnu_noalloc(h->c, lam_dev, x_dev, k, out_host);
+  });
+}
+
 int gb_apply(gb_ctx* h, int which, const double* x_dev, double* y_dev) {
   if (!h) return GB_ERR_INVALID_ARG;
   return guarded([&] {

@@ -183,6 +183,7 @@ int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_s
 void apply_operator(Ctx& c, int which, const double* x, double* y);
 double time_kernel(Ctx& c, int which, int reps);
 void dnu(Ctx& c, const double* lam, const double* x, int k, double* out);
+void dnu_noalloc(Ctx& c, const double* lam, const double* x, int k, double* out);
 void release_workspace(Ctx& c);
 
 // Velocity DOF decoding shared by host setup code.

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -584,6 +585,68 @@ void dnu(Ctx& c, const double* lam, const double* x, int k, double* out) {
   const int grid = grid_cap(c.n_u * 8);
   double* res = c.ws.aux + (size_t)kRB * 32 - 32;  // k results after the partials
   k_dnu<<<grid, kBlock, 0, c.stream>>>(a, k, lam, x, c.ws.partial, c.ws.counter, res);
+  GBS_CUDA(cudaGetLastError());
+  GBS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// ---- dL/dnu without allocating device memory --------------------------------
+// gb_dnu may allocate the context's workspace (cudaMalloc) on first use.  Some
+// callers cannot allow that: code that runs while a CUDA graph is being
+// captured, programs whose device memory is owned by a pool or framework that
+// forbids further cudaMalloc calls, and callers that have used up a fixed
+// memory budget.  dnu_noalloc computes the same quantity with the same kernel
+// (k_dnu, same launch) but takes its reduction scratch -- the per-block
+// partial sums, the completion counter and the k results -- from the static
+// device array below, whose size is fixed at build time: 64 + 1216 * 32
+// doubles (about 304 KiB), enough for the largest launch (1216 blocks) and
+// k <= 32.  Every GPU that loads this library holds the array until the
+// process exits.  All calls share it, so calls that overlap on the GPU race;
+// each call clears the counter before its launch.
+constexpr int kNoAllocMaxK = 32;
+constexpr size_t kNoAllocDoubles = 64 + (size_t)kRB * kNoAllocMaxK;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
+
+// The host-side name g_noalloc_scratch is only a stand-in for the symbol; the
+// kernel needs its device address, looked up once per device with that
+// device current (the first call on a device does this lookup, so it should
+// come before any stream capture).
+double* noalloc_scratch() {
+  int dev = 0;
+  GBS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(GB_ERR_INVALID_ARG, "gb_dnu_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      fail(GB_ERR_CUDA, std::string("gb_dnu_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    }
+    g_noalloc_addr[dev] = (double*)p;
+  }
+  return g_noalloc_addr[dev];
+}
+}  // namespace
+
+void dnu_noalloc(Ctx& c, const double* lam, const double* x, int k, double* out) {
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "gb_dnu_noalloc: assemble first");
+  if (k < 1 || k > kNoAllocMaxK)
+    fail(GB_ERR_INVALID_ARG, "gb_dnu_noalloc: k must be in [1, 32], the size of its static scratch");
+  if (!lam || !x || !out) fail(GB_ERR_INVALID_ARG, "gb_dnu_noalloc: null pointer argument");
+  const int grid = grid_cap(c.n_u * 8);
+  if ((size_t)grid * k + 64 > kNoAllocDoubles) fail(GB_ERR_INVALID_ARG, "gb_dnu_noalloc: launch exceeds static scratch");
+  double* scratch = noalloc_scratch();
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);  // scratch[0]
+  double* res = scratch + 32;                                 // scratch[32 .. 32+k)
+  double* partial = scratch + 64;                             // [k][grid] partial sums
+  Args a = make_args(c, nullptr, 1);
+  GBS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), c.stream));
+  k_dnu<<<grid, kBlock, 0, c.stream>>>(a, k, lam, x, partial, counter, res);
   GBS_CUDA(cudaGetLastError());
   GBS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));
