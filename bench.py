@@ -74,6 +74,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world, steps, k, ms_slowest):
+    """Whole-job solves/s: every rank solves `steps` batches of k right-hand
+    sides; the job takes as long as the slowest rank."""
+    return world * steps * k / (ms_slowest / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
 
@@ -327,13 +343,9 @@ def main():
     torch.cuda.synchronize()
     clock_info = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     infos = info if isinstance(info, list) else [info]
-    value = world * args.steps * k / (ms / 1000.0)
+    value = throughput(world, args.steps, k, ms)
 
     # end to end through the public host-buffer call (pinned memory)
     rhs_h = rhs.cpu().pin_memory()
@@ -344,11 +356,7 @@ def main():
     t = time.perf_counter()
     for _ in range(args.steps):
         s.solve_host(rhs_h, out_h, **opts)
-    e2e_s = time.perf_counter() - t
-    if dist is not None:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t, dist)
     bytes_io = 8 * k * s.n
 
     # per-kernel timing (events on the library's stream) and the roofline
@@ -404,7 +412,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * args.steps * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bytes_io,
+            "e2e": {"value": throughput(world, args.steps, k, 1000.0 * e2e_s), "unit": "solves/s",
+                    "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
             "gpu_launches": int(args.steps * sum(launches_per_solve(s, i) for i in infos)),
             "clocks": clock_info,

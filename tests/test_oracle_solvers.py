@@ -252,6 +252,13 @@ def test_adjoint_gradients_match_central_differences(oracle_mod):
     h = 1e-6
     fd = (loss(nu + h, f) - loss(nu - h, f)) / (2 * h)
     assert abs(fd - g_nu) <= 1e-6 * abs(fd)
+    # B does not depend on nu, so u(nu) = u(1) / nu and p(nu) = p(1): the
+    # gradient has the closed form dL/dnu = -(u - u_t)^T u / nu
+    assert abs(g_nu + (u - ut) @ u / nu) <= 1e-8 * abs(g_nu)
+    x1 = _direct_solve(oracle_mod.Problem(dim, N, p, nu=1.0), f)
+    xd = _direct_solve(P, f)
+    np.testing.assert_allclose(xd[:P.n_u], x1[:P.n_u] / nu, rtol=0, atol=1e-12 * np.abs(x1).max())
+    np.testing.assert_allclose(xd[P.n_u:], x1[P.n_u:], rtol=0, atol=1e-12 * np.abs(x1).max())
     d = rng.standard_normal(P.n_u)
     d /= np.linalg.norm(d)
     eps = 1e-3  # L is quadratic in f: the central difference is exact
