@@ -190,11 +190,15 @@ int gb_dnu_noalloc(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int 
 int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
 /* Kernel layout of single-right-hand-side solves (k == 1) for one precision
- * (GB_PREC_*): spmv / trsv = 0 CSR with 8 lanes per row, 1 SELL-32 with one
- * thread per row, -1 automatic.  Automatic (the default) times both layouts
- * on this problem at the first single-RHS solve of that precision and keeps
- * the faster one; the layouts differ only in the summation order inside a
- * row.  gb_get_kernel_variants reports the current choice (-1: not made). */
+ * (GB_PREC_*).  spmv: 0 CSR with 8 lanes per row, 1 SELL-32 with one thread
+ * per row.  trsv (the IC(0) sweeps): 0 CSR, 1 SELL-32, 2 / 3 / 4 staged (each
+ * block stages its rows of a level in shared memory and gathers the solution
+ * entries they need in one round trip; about 4 / 12 / 32 entries per lane).
+ * -1 automatic.  Automatic (the default) times the layouts on this problem at
+ * the first single-RHS solve of that precision and keeps the fastest; the
+ * layouts differ only in the summation order inside a row.  Values outside
+ * these ranges return GB_ERR_INVALID_ARG.  gb_get_kernel_variants reports the
+ * current choice (-1: not made). */
 int gb_set_kernel_variants(gb_ctx* ctx, int precision, int spmv, int trsv);
 int gb_get_kernel_variants(const gb_ctx* ctx, int precision, int* spmv, int* trsv);
 

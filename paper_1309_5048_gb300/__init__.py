@@ -243,18 +243,21 @@ class Stokes:
         _check(load_library().gb_dnu(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
         return out
 
-    LAYOUTS = {"auto": -1, "csr": 0, "sell": 1}
+    LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
-        """Layout of the single-RHS inner SpMV and IC(0) sweeps: 'csr' (8
-        lanes per row), 'sell' (SELL-32, one thread per row) or 'auto'."""
+        """Layout of the single-RHS inner SpMV ('csr': 8 lanes per row,
+        'sell': SELL-32, one thread per row) and IC(0) sweeps (also 'staged4',
+        'staged12', 'staged32': rows staged in shared memory, about 4/12/32
+        entries per lane), or 'auto'."""
         _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.LAYOUTS[spmv],
                                                       self.LAYOUTS[trsv]))
 
     def kernel_variants(self, precision="fp64"):
         a, b = C.c_int(0), C.c_int(0)
         _check(load_library().gb_get_kernel_variants(self._h, PRECISIONS[precision], C.byref(a), C.byref(b)))
-        names = {-1: "unset", 0: "csr", 1: "sell"}
+        names = {v: k for k, v in self.LAYOUTS.items()}
+        names[-1] = "unset"
         return names[a.value], names[b.value]
 
     KERNELS = {"cg_spmv": 0, "ic0_apply": 1, "stokes_apply": 2, "trsv_fwd": 3}

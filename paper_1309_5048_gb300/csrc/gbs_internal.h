@@ -79,6 +79,23 @@ struct Sell {
   int nslices = 0;
 };
 
+// Block partition of the levels of one triangular sweep for the staged
+// single-RHS kernels: every block owns a contiguous range of internal rows of
+// one level, at most kStagedRows rows and kStagedEntries off-diagonal
+// entries, and the blocks of a level are balanced by entries over a grid of
+// (a multiple of) the SM count.  Block b of the sweep is described by
+// desc[4b .. 4b+3] = {first row, end row, first entry, end entry} (CSR
+// positions); level l owns blocks lev_b[l] ... lev_b[l] + lev_nb[l] - 1.
+constexpr int kStagedRows = 256;
+constexpr int kStagedEntries = 2048;
+struct Staged {
+  DevBuf<int32_t> desc;
+  std::vector<int32_t> lev_b, lev_nb;
+  std::vector<int32_t> lev_ecap, lev_rcap;  // largest block of the level (entries, rows)
+  std::vector<float> lev_mean;             // mean off-diagonal entries per row
+  int ecap = 0, rcap = 0;                  // over all levels
+};
+
 struct Workspace {
   int K = 0;          // padded batch width
   int k = 0;          // capacity (right-hand sides) of the staging buffers
@@ -155,9 +172,12 @@ struct Ctx {
   DevBuf<double> tab1d;  // 1D integral tables (assembly)
   Sell sA, sL, sU;                 // SELL-32 copies of A, L, U
   std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
+  Staged tL, tU;                   // staged-sweep partitions of L and U = L^T
+  int n_sm = 0;                    // streaming multiprocessors of the device
   // kernel layout per precision (index 0 FP64, 1 mixed) for single-RHS
-  // solves: 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row, -1 not
-  // chosen yet (timed at the first single-RHS solve)
+  // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row;
+  // triangular sweeps 0 CSR, 1 SELL-32, 2/3/4 staged with about 4/12/32
+  // entries per lane; -1 not chosen yet (timed at the first single-RHS solve)
   int var_spmv[2] = {-1, -1}, var_trsv[2] = {-1, -1};
   DevBuf<int> status_d;  // device error flags
   double nu = 1.0, cpen = 0.0;

@@ -307,6 +307,63 @@ void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col
   S.val32.alloc(std::max<int64_t>(1, slots));
 }
 
+// Block partition of each level of a sweep over the CSR pattern (ptr) for the
+// staged kernels (Staged in gbs_internal.h).  A level gets about
+// max(ceil(entries / kStagedEntries), ceil(rows / kStagedRows)) blocks,
+// raised to the SM count (or to a multiple of it), and rows are cut greedily
+// at equal shares of entries + 4 per row; a block never exceeds the caps.
+void build_staged(const std::vector<int32_t>& ptr, const std::vector<int32_t>& lev_ptr, int n_sm,
+                  Staged& T, cudaStream_t stream) {
+  const int nlev = (int)lev_ptr.size() - 1;
+  std::vector<int32_t> brow, desc;
+  T.lev_b.assign(nlev, 0);
+  T.lev_nb.assign(nlev, 0);
+  T.lev_ecap.assign(nlev, 0);
+  T.lev_rcap.assign(nlev, 0);
+  T.lev_mean.assign(nlev, 0.f);
+  T.ecap = T.rcap = 0;
+  for (int l = 0; l < nlev; ++l) {
+    const int32_t r0 = lev_ptr[l], r1 = lev_ptr[l + 1];
+    const int64_t R = r1 - r0, E = (int64_t)ptr[r1] - ptr[r0];
+    int64_t nb = std::max<int64_t>((E + kStagedEntries - 1) / kStagedEntries, (R + kStagedRows - 1) / kStagedRows);
+    nb = nb <= n_sm ? std::min<int64_t>(R, n_sm) : (nb + n_sm - 1) / n_sm * n_sm;
+    const double share = (double)(E + 4 * R) / (double)std::max<int64_t>(1, nb);
+    T.lev_b[l] = (int32_t)(desc.size() / 4);
+    T.lev_mean[l] = R ? (float)((double)E / (double)R) : 0.f;
+    brow.assign(1, r0);
+    int64_t acc = 0, ent = 0, rows = 0, cuts = 0;
+    for (int32_t r = r0; r < r1; ++r) {
+      const int64_t len = ptr[r + 1] - ptr[r];
+      if (len > kStagedEntries) fail(GB_ERR_INVALID_ARG, "row too long for the staged sweep");
+      const bool full = ent + len > kStagedEntries || rows == kStagedRows;
+      const bool due = rows > 0 && (double)(acc + len + 4) > share * (double)(cuts + 1);
+      if (rows > 0 && (full || due)) {
+        brow.push_back(r);
+        T.lev_ecap[l] = std::max<int32_t>(T.lev_ecap[l], (int32_t)ent);
+        T.lev_rcap[l] = std::max<int32_t>(T.lev_rcap[l], (int32_t)rows);
+        ++cuts;
+        ent = rows = 0;
+      }
+      acc += len + 4;
+      ent += len;
+      ++rows;
+    }
+    brow.push_back(r1);
+    T.lev_ecap[l] = std::max<int32_t>(T.lev_ecap[l], (int32_t)ent);
+    T.lev_rcap[l] = std::max<int32_t>(T.lev_rcap[l], (int32_t)rows);
+    T.lev_nb[l] = (int32_t)(cuts + 1);
+    T.ecap = std::max(T.ecap, T.lev_ecap[l]);
+    T.rcap = std::max(T.rcap, T.lev_rcap[l]);
+    for (size_t b = 0; b + 1 < brow.size(); ++b) {
+      desc.push_back(brow[b]);
+      desc.push_back(brow[b + 1]);
+      desc.push_back(ptr[brow[b]]);
+      desc.push_back(ptr[brow[b + 1]]);
+    }
+  }
+  T.desc.upload(desc.data(), desc.size(), stream);
+}
+
 }  // namespace
 
 void setup_pattern(Ctx& c, const gb_problem& prob) {
@@ -504,6 +561,13 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   build_sell(c.hA_ptr, c.hA_col, c.lev_ptr, c.lev_slice, c.sA, s);
   build_sell(Lptr, Lcol, c.lev_ptr, c.lev_slice, c.sL, s);
   build_sell(Uptr, Ucol, c.lev_ptr, c.lev_slice, c.sU, s);
+  {
+    int dev = 0;
+    GBS_CUDA(cudaGetDevice(&dev));
+    GBS_CUDA(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  build_staged(Lptr, c.lev_ptr, c.n_sm, c.tL, s);
+  build_staged(Uptr, c.lev_ptr, c.n_sm, c.tU, s);
   c.status_d.alloc(16);
   c.status_d.zero(s);
   GBS_CUDA(cudaStreamSynchronize(s));

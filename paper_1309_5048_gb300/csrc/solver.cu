@@ -157,6 +157,47 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   return a;
 }
 
+// Dynamic shared memory of k_trsv_level_staged for a block of at most ecap
+// entries and rcap rows.
+size_t staged_smem_bytes(int ecap, int rcap, size_t tsize) {
+  return (size_t)(2 * ecap + 2 * rcap) * tsize + (size_t)(ecap + rcap + 1) * 4;
+}
+
+template <class T, bool FWD, int G>
+void staged_allow_smem_one(size_t bytes) {
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_staged<T, FWD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes));
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_staged<T, FWD, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+}
+
+template <class T, bool FWD>
+void staged_allow_smem(size_t bytes) {
+  staged_allow_smem_one<T, FWD, 1>(bytes);
+  staged_allow_smem_one<T, FWD, 2>(bytes);
+  staged_allow_smem_one<T, FWD, 4>(bytes);
+  staged_allow_smem_one<T, FWD, 8>(bytes);
+  staged_allow_smem_one<T, FWD, 16>(bytes);
+  staged_allow_smem_one<T, FWD, 32>(bytes);
+}
+
+// Shared memory of every staged launch of this problem: one size for all
+// levels and both sweeps, with the carve-out fixed at its shared-memory
+// maximum, so consecutive levels never ask the SMs for a different L1 /
+// shared split (a change that cannot overlap the previous level).
+template <class T>
+size_t staged_bytes(const Ctx& c) {
+  return staged_smem_bytes(std::max(c.tL.ecap, c.tU.ecap), std::max(c.tL.rcap, c.tU.rcap), sizeof(T));
+}
+
+// Raise the dynamic shared-memory limit of the staged sweep kernels to what
+// the partitions of this problem need (outside any graph capture).
+template <class T>
+void staged_prepare(Ctx& c) {
+  staged_allow_smem<T, true>(staged_bytes<T>(c));
+  staged_allow_smem<T, false>(staged_bytes<T>(c));
+}
+
 int grid_cap(int64_t threads) {
   int64_t g = (threads + kBlock - 1) / kBlock;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, kRB));
@@ -167,7 +208,7 @@ struct Run {
   Ctx& c;
   Args a;
   cudaStream_t s;
-  int vspmv = 0, vtrsv = 0;  // single-RHS layout: 0 CSR (8 lanes per row), 1 SELL-32
+  int vspmv = 0, vtrsv = 0;  // single-RHS layouts (Ctx::var_spmv, Ctx::var_trsv)
   static constexpr int G = Map<K>::G;
   Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {
     const int pi = std::is_same<T, float>::value ? 1 : 0;
@@ -183,8 +224,38 @@ struct Run {
   void update() { k_update<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a); }
   // One kernel per level, launched with programmatic dependent launch so a
   // level's independent loads overlap the previous level (k_trsv_level).
+  template <bool FWD, int GG>
+  void staged_level(cudaLaunchConfig_t& cfg, const Staged& st, int l) {
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_staged<T, FWD, GG>, a, (const int4*)st.desc.p + st.lev_b[l],
+                                std::max(c.tL.ecap, c.tU.ecap), std::max(c.tL.rcap, c.tU.rcap)));
+  }
   template <bool FWD>
   void level(int l) {
+    if (K == 1 && vtrsv >= 2) {
+      const Staged& st = FWD ? c.tL : c.tU;
+      const float per_lane = vtrsv == 2 ? 4.f : (vtrsv == 3 ? 12.f : 32.f);
+      int lanes = 1;
+      while (lanes < 32 && st.lev_mean[l] > per_lane * (float)lanes) lanes *= 2;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)st.lev_nb[l]);
+      cfg.blockDim = dim3(kBlock);
+      cfg.dynamicSmemBytes = staged_bytes<T>(c);
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      switch (lanes) {
+        case 1: staged_level<FWD, 1>(cfg, st, l); break;
+        case 2: staged_level<FWD, 2>(cfg, st, l); break;
+        case 4: staged_level<FWD, 4>(cfg, st, l); break;
+        case 8: staged_level<FWD, 8>(cfg, st, l); break;
+        case 16: staged_level<FWD, 16>(cfg, st, l); break;
+        default: staged_level<FWD, 32>(cfg, st, l); break;
+      }
+      return;
+    }
     const bool sell = (K == 1 && vtrsv == 1);
     const int r0 = sell ? c.lev_slice[l] : c.lev_ptr[l];
     const int r1 = sell ? c.lev_slice[l + 1] : c.lev_ptr[l + 1];
@@ -335,13 +406,15 @@ struct Run {
 };
 
 // Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
-// SELL-32 (thread per row) forms of the inner SpMV and of one IC(0)
-// application on this problem and keep the faster; SELL must win by 3% to
-// replace CSR.  Runs once per precision, outside any graph capture; the
-// choice only changes the summation order inside a row.
+// SELL-32 (thread per row) forms of the inner SpMV, and the CSR, SELL-32 and
+// three staged forms (about 4, 12, 32 entries per lane) of one IC(0)
+// application, on this problem, and keep the fastest; a form replaces the
+// best so far only when it is 3% faster.  Runs once per precision, outside
+// any graph capture; the choice only changes the summation order inside a row.
 template <class T>
 void autotune_single(Ctx& c) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
+  staged_prepare<T>(c);
   if (c.var_spmv[pi] >= 0 && c.var_trsv[pi] >= 0) return;
   Workspace& w = c.ws;
   k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_p, c.n_u, T(1));
@@ -355,8 +428,8 @@ void autotune_single(Ctx& c) {
   GBS_CUDA(cudaEventCreate(&e1));
   auto time_it = [&](int variant, int which) {
     Run<1, T> run(c, a);
-    run.vspmv = variant;
-    run.vtrsv = variant;
+    if (which == 0) run.vspmv = variant;
+    else run.vtrsv = variant;
     const int reps = which == 0 ? 20 : 5;
     auto launch = [&] {
       if (which == 0) run.spmv();
@@ -375,7 +448,18 @@ void autotune_single(Ctx& c) {
     return ms;
   };
   if (c.var_spmv[pi] < 0) c.var_spmv[pi] = time_it(1, 0) < 0.97f * time_it(0, 0) ? 1 : 0;
-  if (c.var_trsv[pi] < 0) c.var_trsv[pi] = time_it(1, 1) < 0.97f * time_it(0, 1) ? 1 : 0;
+  if (c.var_trsv[pi] < 0) {
+    float best = time_it(0, 1);
+    int choice = 0;
+    for (int v = 1; v <= 4; ++v) {
+      const float t = time_it(v, 1);
+      if (t < 0.97f * best) {
+        best = t;
+        choice = v;
+      }
+    }
+    c.var_trsv[pi] = choice;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   GBS_CUDA(cudaGetLastError());

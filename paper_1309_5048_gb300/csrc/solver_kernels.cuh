@@ -574,7 +574,10 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level(Args a, int r0, int r1) {
     ii = inv[row];
   }
   cudaGridDependencySynchronize();
-  if (!act || SF(a, S_CG_ACTIVE, t, K) == 0.0) return;  // uniform over a lane group
+  if (!act) return;  // uniform over a lane group
+  // the CG state flag is loaded together with the solution entries and only
+  // decides the store (uniform over a lane group)
+  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
   T s = 0;
 #pragma unroll
   for (int u = 0; u < PF; ++u)
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level(Args a, int r0, int r1) {
     else s = (T)group_sumf<M::G>((float)s);
   }
   const size_t ridx = (K == 1) ? (size_t)row : (size_t)row * K + t;
-  if (K > 1 || g == 0) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
+  if (live && (K > 1 || g == 0)) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
 }
 
 // ---- SELL-32 variants (single right-hand side, one thread per row) --------
@@ -661,13 +664,116 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
     ii = inv[row];
   }
   cudaGridDependencySynchronize();
-  if (!act || SF(a, S_CG_ACTIVE, 0, 1) == 0.0) return;
+  if (!act) return;
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the store only
   T sum = 0;
 #pragma unroll
   for (int k = 0; k < PF; ++k)
     if (k < len) sum += v[k] * __ldcg(out + cc[k]);
   for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
-  out[row] = (__ldcg(rhs + row) - sum) * ii;
+  if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
+}
+
+// ---- staged variant (single right-hand side) ------------------------------
+// One level of a triangular solve (same recurrences as k_trsv_level) over a
+// block partition of the level (build_staged): block b owns the contiguous
+// rows [desc[4b], desc[4b+1]), whose off-diagonal entries are the contiguous
+// CSR positions [desc[4b+2], desc[4b+3]).  Before the wait for the previous level the block copies the
+// rows' column indices, factor values, row offsets and 1/L_ii into shared
+// memory with coalesced loads (this overlaps the previous level).  After the
+// wait all threads gather the needed solution entries at once -- one
+// memory round trip per level, whatever the row lengths -- and then G lanes
+// per row sum value * entry from shared memory, G chosen by the host from
+// the level's mean row length.  Dynamic shared memory: T val[ecap], T
+// xg[ecap], T rhs[rcap], T inv[rcap], int col[ecap], int off[rcap + 1].
+template <class T, bool FWD, int G>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_staged(Args a, const int4* __restrict__ desc, int ecap,
+                                                              int rcap) {
+  constexpr int EPT = kStagedEntries / kBlock;  // entries per thread
+  static_assert(EPT * kBlock == kStagedEntries && kStagedRows <= kBlock, "staged block shape");
+  extern __shared__ __align__(16) unsigned char staged_smem[];
+  cudaTriggerProgrammaticLaunchCompletion();
+  const int32_t* __restrict__ ptr = FWD ? a.L_ptr : a.U_ptr;
+  const int32_t* __restrict__ col = FWD ? a.L_col : a.U_col;
+  const T* __restrict__ val = FWD ? pick<T>(a.L_val, a.L_val32) : pick<T>(a.U_val, a.U_val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  T* sv = (T*)staged_smem;
+  T* sx = sv + ecap;
+  T* sr = sx + ecap;
+  T* si = sr + rcap;
+  int* sc = (int*)(si + rcap);
+  int* so = sc + ecap;
+  const int tid = threadIdx.x;
+  const int4 d = desc[blockIdx.x];
+  const int rb = d.x, nr = d.y - d.x;
+  const int eb = d.z, ne = d.w - d.z;
+  {
+    // all loads first (one round trip), then the shared-memory stores
+    int cv[EPT];
+    T vv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = tid + u * kBlock;
+      cv[u] = e < ne ? col[eb + e] : 0;
+      vv[u] = e < ne ? val[eb + e] : T(0);
+    }
+    const int o = tid < nr ? ptr[rb + tid] - eb : 0;
+    const T iv = tid < nr ? inv[rb + tid] : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = tid + u * kBlock;
+      if (e < ne) {
+        sc[e] = cv[u];
+        sv[e] = vv[u];
+      }
+    }
+    if (tid < nr) {
+      so[tid] = o;
+      si[tid] = iv;
+    }
+    if (tid == 0) so[nr] = ne;
+  }
+  cudaGridDependencySynchronize();
+  __syncthreads();
+  // the CG state flag is read together with the gathers; it only decides the
+  // stores (uniform over the grid)
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;
+  {
+    T xv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = tid + u * kBlock;
+      xv[u] = e < ne ? __ldcg(out + sc[e]) : T(0);
+    }
+    const T rv = tid < nr ? __ldcg(rhs + rb + tid) : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = tid + u * kBlock;
+      if (e < ne) sx[e] = xv[u];
+    }
+    if (tid < nr) sr[tid] = rv;
+  }
+  __syncthreads();
+  if (!live) return;
+  const int g = tid % G;
+  for (int i = tid / G; i < nr; i += kBlock / G) {  // uniform over a lane group
+    const int e1 = so[i + 1];
+    int e = so[i] + g;
+    T s0 = 0, s1 = 0;
+    for (; e + G < e1; e += 2 * G) {
+      s0 += sv[e] * sx[e];
+      s1 += sv[e + G] * sx[e + G];
+    }
+    if (e < e1) s0 += sv[e] * sx[e];
+    T s = s0 + s1;
+    if (G > 1) {
+      if (sizeof(T) == 8) s = (T)group_sum<G>((double)s);
+      else s = (T)group_sumf<G>((float)s);
+    }
+    if (g == 0) out[rb + i] = (sr[i] - s) * si[i];
+  }
 }
 
 // x[i] = v (kernel timing and layout tuning only).

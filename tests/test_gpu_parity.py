@@ -290,11 +290,17 @@ def test_edge_cases(oracle_mod, gb):
         gb.Stokes(4, 3, 3)
 
 
-@pytest.mark.parametrize("spmv,trsv", [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr")])
-@pytest.mark.parametrize("dim,N,p", [(2, 13, 3), (3, 3, 3)])
+LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr"), ("csr", "staged4"),
+                ("sell", "staged12"), ("csr", "staged32")]
+
+
+@pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
+@pytest.mark.parametrize("dim,N,p", [(2, 13, 3), (3, 3, 3), (2, 40, 4)])
 def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p):
-    """Both single-RHS layouts (CSR 8 lanes per row, SELL-32 thread per row)
-    of the inner SpMV and the IC(0) sweeps reproduce the oracle (<= 1e-10)."""
+    """Every single-RHS layout of the inner SpMV (CSR 8 lanes per row,
+    SELL-32 thread per row) and of the IC(0) sweeps (also the staged forms,
+    whose levels are split over many blocks at 2D 40^2) reproduces the
+    oracle (<= 1e-10)."""
     ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
     assert ref.factor() < 0
     s.factor_ic0()
@@ -316,7 +322,8 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     assert s.kernel_variants("fp64") == ("unset", "unset")
     _, rhs = _rhs(oracle_mod.Problem(2, 20, 3), s, "fourier", seed=3)
     s.solve(rhs, tol=1e-6)
-    assert all(v in ("csr", "sell") for v in s.kernel_variants("fp64"))
+    spmv, trsv = s.kernel_variants("fp64")
+    assert spmv in ("csr", "sell") and trsv in ("csr", "sell", "staged4", "staged12", "staged32")
 
 
 @pytest.mark.slow
