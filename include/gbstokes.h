@@ -99,7 +99,8 @@ typedef struct {
   int inner_its_max;   /* largest inner count of one application */
   double relres_est;   /* |eta| / gamma_1 at exit */
   double relres_true;  /* ||b - K x||_2 / ||b||_2 recomputed at exit */
-  int status;          /* GB_OK, GB_ERR_NOT_CONVERGED or GB_ERR_NONFINITE */
+  int status;          /* GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_NONFINITE or
+                          GB_ERR_INVALID_ARG (inconsistent pressure rhs) */
 } gb_info;
 
 /* ---------------------------------------------------------------- setup --
@@ -144,10 +145,13 @@ int gb_factor_ic0(gb_ctx* ctx, int64_t* breakdown_row_host);
 /* Preconditioned MINRES (Sec. 5) on K x = b, K = [A_h B^T; B 0], for k
  * right-hand sides at once, from x_0 = 0.  rhs_dev: [k][n_u + n_p] doubles;
  * the pressure part of each rhs must satisfy 1^T g_p = 0 (K is singular with
- * kernel [0; 1]); the pressure of x is filtered to zero mean,
- * p <- p - (w^T p / w^T 1) 1 (Sec. 6.4).  x_dev: [k][n_u + n_p].  info_host:
- * k entries.  Returns GB_ERR_NOT_CONVERGED if a RHS hit max_outer (its x is
- * still written), GB_ERR_NONFINITE if a NaN/Inf was met. */
+ * kernel [0; 1]); a rhs with |1^T g_p| > 1e-10 sqrt(n_p) ||g_p||_2 is not
+ * solved (its x is zero, its info status GB_ERR_INVALID_ARG).  The pressure
+ * of x is filtered to zero mean, p <- p - (w^T p / w^T 1) 1 (Sec. 6.4).
+ * x_dev: [k][n_u + n_p].  info_host: k entries, status GB_OK,
+ * GB_ERR_NOT_CONVERGED (max_outer reached; x still written),
+ * GB_ERR_NONFINITE (NaN/Inf met) or GB_ERR_INVALID_ARG.  The call returns the
+ * most severe per-rhs status (nonfinite > invalid > not converged). */
 int gb_solve(gb_ctx* ctx, const double* rhs_dev, double* x_dev, int k,
              const gb_solve_opts* opts, gb_info* info_host);
 

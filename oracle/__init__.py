@@ -56,29 +56,36 @@ def lib():
             vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
             L.or_last_error.restype = C.c_char_p
             L.or_create.restype = vp
-            L.or_create.argtypes = [i32, i32, i32, dbl, dbl, i32, vp, vp]
+            L.or_create.argtypes = [i32, i32, i32, dbl, dbl, i32, i32, vp, vp]
             L.or_destroy.argtypes = [vp]
             for name in ("or_sizes", "or_csr", "or_wmean", "or_perm", "or_load_fourier",
                          "or_load_manufactured", "or_manufactured_errors", "or_minres",
-                         "or_pcg", "or_precond", "or_stokes_apply", "or_filter"):
+                         "or_pcg", "or_precond", "or_stokes_apply", "or_filter", "or_perm_q",
+                         "or_pcg_q"):
                 getattr(L, name).restype = i32
             L.or_sizes.argtypes = [vp, vp]
             L.or_csr.argtypes = [vp, i32, vp, vp, vp]
             L.or_wmean.argtypes = [vp, vp]
             L.or_perm.argtypes = [vp, vp, vp, vp]
+            L.or_perm_q.argtypes = [vp, vp, vp, vp]
             L.or_factor.restype = i64
             L.or_factor.argtypes = [vp]
+            L.or_factor_q.restype = i64
+            L.or_factor_q.argtypes = [vp]
             L.or_load_fourier.argtypes = [vp, i32, vp, vp, vp]
             L.or_load_manufactured.argtypes = [vp, vp]
             L.or_manufactured_errors.argtypes = [vp, vp, vp, vp]
             L.or_manufactured_point.argtypes = [dbl, dbl, dbl, vp]
-            L.or_minres.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, vp, i64, vp]
+            L.or_minres.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, vp, i64, i32, vp, i64, vp]
             L.or_counts.restype = i64
             L.or_counts.argtypes = [vp, vp, i64]
+            L.or_qcounts.restype = i64
+            L.or_qcounts.argtypes = [vp, vp, i64]
             L.or_hist.restype = i64
             L.or_hist.argtypes = [vp, vp, i64]
             L.or_pcg.argtypes = [vp, vp, vp, dbl, i32]
-            L.or_precond.argtypes = [vp, vp, vp, dbl, i32]
+            L.or_pcg_q.argtypes = [vp, vp, vp, dbl, i32]
+            L.or_precond.argtypes = [vp, vp, vp, dbl, i32, i32]
             L.or_stokes_apply.argtypes = [vp, vp, vp]
             L.or_filter.argtypes = [vp, vp]
             L.or_dnu.restype = dbl
@@ -93,6 +100,9 @@ def _p(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
+PRESSURE_BLOCKS = {"diag": 0, "pcg": 1}
+
+
 def default_cpen(p: int) -> float:
     """C_pen = 5(k'+1) with k' = p-1 (Sec. 6.2)."""
     return 5.0 * p
@@ -103,11 +113,14 @@ class Problem:
 
     dim 2 or 3, N elements per direction, velocity degree p (pressure degree
     k' = p-1), viscosity nu, Nitsche constant cpen (None -> 5(k'+1)), ordering
-    of A before IC(0).  ``rows_u`` / ``rows_p`` (boolean masks) restrict the
-    assembly to sampled rows of a large problem (no ordering or factor then).
+    of A before IC(0), qordering of Q before its IC(0) (natural: the factor
+    is then exact, see factor_q).  ``rows_u`` / ``rows_p`` (boolean masks)
+    restrict the assembly to sampled rows of a large problem (no ordering or
+    factor then).
     """
 
-    def __init__(self, dim, N, p, nu=1.0, cpen=None, ordering="natural", rows_u=None, rows_p=None):
+    def __init__(self, dim, N, p, nu=1.0, cpen=None, ordering="natural", rows_u=None, rows_p=None,
+                 qordering="natural"):
         L = lib()
         self.dim, self.N, self.p, self.nu = dim, N, p, float(nu)
         self.cpen = default_cpen(p) if cpen is None else float(cpen)
@@ -120,15 +133,17 @@ class Problem:
                 su = np.zeros(n_u, np.int8)
             if sp is None:
                 sp = np.zeros(n_p, np.int8)
-        h = L.or_create(dim, N, p, self.nu, self.cpen, ORDERINGS[ordering], _p(su), _p(sp))
+        h = L.or_create(dim, N, p, self.nu, self.cpen, ORDERINGS[ordering], ORDERINGS[qordering],
+                        _p(su), _p(sp))
         if not h:
             raise RuntimeError(L.or_last_error().decode())
         self._h = h
-        s = np.zeros(8, np.int64)
+        s = np.zeros(11, np.int64)
         L.or_sizes(h, _p(s))
         (self.n_u, self.n_p, self.nnzA, self.nnzB, self.nnzQ, self.nnzL,
-         self.nlevels, self.nrlevels) = (int(v) for v in s)
+         self.nlevels, self.nrlevels, self.nnzLQ, self.nqlevels, self.nqrlevels) = (int(v) for v in s)
         self.factored = False
+        self.qfactored = False
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -138,10 +153,11 @@ class Problem:
 
     # --- matrices ---------------------------------------------------------
     def csr(self, which):
-        """('A'|'B'|'Q'|'L') -> (indptr int64, indices int32, data float64)."""
-        w = {"A": 0, "B": 1, "Q": 2, "L": 3}[which]
-        nrows = {"A": self.n_u, "B": self.n_p, "Q": self.n_p, "L": self.n_u}[which]
-        nnz = {"A": self.nnzA, "B": self.nnzB, "Q": self.nnzQ, "L": self.nnzL}[which]
+        """('A'|'B'|'Q'|'L'|'LQ') -> (indptr int64, indices int32, data float64).
+        L and LQ are the IC(0) factors of A and Q in their orderings."""
+        w = {"A": 0, "B": 1, "Q": 2, "L": 3, "LQ": 4}[which]
+        nrows = {"A": self.n_u, "B": self.n_p, "Q": self.n_p, "L": self.n_u, "LQ": self.n_p}[which]
+        nnz = {"A": self.nnzA, "B": self.nnzB, "Q": self.nnzQ, "L": self.nnzL, "LQ": self.nnzLQ}[which]
         ptr = np.zeros(nrows + 1, np.int64)
         col = np.zeros(nnz, np.int32)
         val = np.zeros(nnz, np.float64)
@@ -151,7 +167,7 @@ class Problem:
     def scipy(self, which):
         import scipy.sparse as sp
         ptr, col, val = self.csr(which)
-        ncols = {"A": self.n_u, "B": self.n_u, "Q": self.n_p, "L": self.n_u}[which]
+        ncols = {"A": self.n_u, "B": self.n_u, "Q": self.n_p, "L": self.n_u, "LQ": self.n_p}[which]
         return sp.csr_matrix((val, col, ptr), shape=(len(ptr) - 1, ncols))
 
     def wmean(self):
@@ -167,11 +183,27 @@ class Problem:
         lib().or_perm(self._h, _p(perm), _p(lev), _p(rlev))
         return perm, lev, rlev
 
+    def ordering_arrays_q(self):
+        """Ordering of the pressure space before IC(0) of Q: (perm, level, rlevel)."""
+        perm = np.zeros(self.n_p, np.int32)
+        lev = np.zeros(self.n_p, np.int32)
+        rlev = np.zeros(self.n_p, np.int32)
+        lib().or_perm_q(self._h, _p(perm), _p(lev), _p(rlev))
+        return perm, lev, rlev
+
     def factor(self):
         r = lib().or_factor(self._h)
         if r == -99:
             raise RuntimeError(lib().or_last_error().decode())
         self.factored = r < 0
+        return int(r)
+
+    def factor_q(self):
+        """IC(0) of the reordered pressure mass matrix Q (Sec. 6.4)."""
+        r = lib().or_factor_q(self._h)
+        if r == -99:
+            raise RuntimeError(lib().or_last_error().decode())
+        self.qfactored = r < 0
         return int(r)
 
     # --- loads --------------------------------------------------------------
@@ -204,28 +236,37 @@ class Problem:
         lib().or_stokes_apply(self._h, _p(x), _p(y))
         return y
 
-    def minres(self, b, tol=1e-8, inner_tol=1e-2, max_outer=5000, max_inner=1000, forced=None):
+    def minres(self, b, tol=1e-8, inner_tol=1e-2, max_outer=5000, max_inner=1000, forced=None,
+               pressure="diag", forced_q=None):
         """Preconditioned MINRES from x0 = 0; pressure filtered to zero mean.
-        Returns (x, info dict with outer, relres_est, relres_true, status,
-        counts (inner its per preconditioner application), hist)."""
-        if not self.factored:
-            raise RuntimeError("factor() first")
+        pressure: 'diag' (Diag(Q_nu)) or 'pcg' (IC(0)-PCG on Q_nu, needs
+        factor_q()).  Returns (x, info dict with outer, relres_est,
+        relres_true, status, counts (inner its per preconditioner
+        application), qcounts (pressure CG its per application), hist)."""
+        if not self.factored or (pressure == "pcg" and not self.qfactored):
+            raise RuntimeError("factor() (and factor_q() for pressure='pcg') first")
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         info = np.zeros(4)
         fc = None if forced is None else np.ascontiguousarray(forced, dtype=np.int32)
+        fq = None if forced_q is None else np.ascontiguousarray(forced_q, dtype=np.int32)
         rc = lib().or_minres(self._h, _p(b), _p(x), tol, inner_tol, max_outer, max_inner,
-                             _p(fc), 0 if fc is None else len(fc), _p(info))
+                             _p(fc), 0 if fc is None else len(fc), PRESSURE_BLOCKS[pressure],
+                             _p(fq), 0 if fq is None else len(fq), _p(info))
         if rc != 0:
             raise RuntimeError(lib().or_last_error().decode())
         n = lib().or_counts(self._h, None, 0)
         counts = np.zeros(max(n, 1), np.int32)
         lib().or_counts(self._h, _p(counts), n)
+        nq = lib().or_qcounts(self._h, None, 0)
+        qcounts = np.zeros(max(nq, 1), np.int32)
+        lib().or_qcounts(self._h, _p(qcounts), nq)
         nh = lib().or_hist(self._h, None, 0)
         hist = np.zeros(max(nh, 1))
         lib().or_hist(self._h, _p(hist), nh)
         return x, dict(outer=int(info[0]), relres_est=float(info[1]), relres_true=float(info[2]),
-                       status=int(info[3]), counts=counts[:n].copy(), hist=hist[:nh].copy())
+                       status=int(info[3]), counts=counts[:n].copy(), qcounts=qcounts[:nq].copy(),
+                       hist=hist[:nh].copy())
 
     def pcg(self, b, inner_tol, max_inner=1000):
         b = np.ascontiguousarray(b, dtype=np.float64)
@@ -233,10 +274,19 @@ class Problem:
         its = lib().or_pcg(self._h, _p(b), _p(x), inner_tol, max_inner)
         return x, int(its)
 
-    def precond(self, r, inner_tol, max_inner=1000):
+    def pcg_q(self, b, inner_tol, max_inner=1000):
+        """IC(0)-preconditioned CG on Q from x0 = 0 (needs factor_q())."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        its = lib().or_pcg_q(self._h, _p(b), _p(x), inner_tol, max_inner)
+        if its < 0:
+            raise RuntimeError(lib().or_last_error().decode())
+        return x, int(its)
+
+    def precond(self, r, inner_tol, max_inner=1000, pressure="diag"):
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros_like(r)
-        its = lib().or_precond(self._h, _p(r), _p(z), inner_tol, max_inner)
+        its = lib().or_precond(self._h, _p(r), _p(z), inner_tol, max_inner, PRESSURE_BLOCKS[pressure])
         return z, int(its)
 
     def filter(self, pres):

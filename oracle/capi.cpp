@@ -20,6 +20,12 @@ struct Handle {
   bool factored = false;
   std::vector<int32_t> counts;
   std::vector<double> hist;
+  // pressure mass matrix: ordering, IC(0) factor and its levels
+  std::vector<int32_t> permQ;
+  Csr LQ;
+  std::vector<int32_t> levelQ, rlevelQ;
+  bool qfactored = false;
+  std::vector<int32_t> qcounts;
 };
 thread_local std::string g_err;
 }  // namespace
@@ -36,8 +42,8 @@ extern "C" {
 
 const char* or_last_error() { return g_err.c_str(); }
 
-void* or_create(int dim, int N, int p, double nu, double cpen, int ordering, const char* sel_u,
-                const char* sel_p) {
+void* or_create(int dim, int N, int p, double nu, double cpen, int ordering, int qordering,
+                const char* sel_u, const char* sel_p) {
   try {
     Handle* h = new Handle();
     h->ordering = ordering;
@@ -71,6 +77,9 @@ void* or_create(int dim, int N, int p, double nu, double cpen, int ordering, con
       make_ordering(h->P, ordering, h->perm);
       lower_pattern(h->P.A, h->perm, h->L);
       level_sets(h->L, h->level, h->rlevel);
+      make_pressure_ordering(h->P, qordering, h->permQ);
+      lower_pattern(h->P.Q, h->permQ, h->LQ);
+      level_sets(h->LQ, h->levelQ, h->rlevelQ);
     }
     return h;
   } catch (const std::exception& e) {
@@ -94,12 +103,18 @@ int or_sizes(void* hv, int64_t* out) {
   for (int32_t v : h->rlevel) mr = v > mr ? v : mr;
   out[6] = ml + 1;
   out[7] = mr + 1;
+  out[8] = h->LQ.nnz();
+  ml = mr = -1;
+  for (int32_t v : h->levelQ) ml = v > ml ? v : ml;
+  for (int32_t v : h->rlevelQ) mr = v > mr ? v : mr;
+  out[9] = ml + 1;
+  out[10] = mr + 1;
   return 0;
 }
 
 int or_csr(void* hv, int which, int64_t* ptr, int32_t* col, double* val) {
   Handle* h = static_cast<Handle*>(hv);
-  const Csr* M = which == 0 ? &h->P.A : which == 1 ? &h->P.B : which == 2 ? &h->P.Q : &h->L;
+  const Csr* M = which == 0 ? &h->P.A : which == 1 ? &h->P.B : which == 2 ? &h->P.Q : which == 3 ? &h->L : &h->LQ;
   if (ptr) std::memcpy(ptr, M->ptr.data(), sizeof(int64_t) * (M->nrows + 1));
   if (col) std::memcpy(col, M->col.data(), sizeof(int32_t) * M->nnz());
   if (val) std::memcpy(val, M->val.data(), sizeof(double) * M->nnz());
@@ -119,6 +134,28 @@ int or_perm(void* hv, int32_t* perm, int32_t* level, int32_t* rlevel) {
   if (level) std::memcpy(level, h->level.data(), sizeof(int32_t) * n);
   if (rlevel) std::memcpy(rlevel, h->rlevel.data(), sizeof(int32_t) * n);
   return 0;
+}
+
+int or_perm_q(void* hv, int32_t* perm, int32_t* level, int32_t* rlevel) {
+  Handle* h = static_cast<Handle*>(hv);
+  int64_t n = h->P.n_p;
+  if (perm) std::memcpy(perm, h->permQ.data(), sizeof(int32_t) * n);
+  if (level) std::memcpy(level, h->levelQ.data(), sizeof(int32_t) * n);
+  if (rlevel) std::memcpy(rlevel, h->rlevelQ.data(), sizeof(int32_t) * n);
+  return 0;
+}
+
+// IC(0) of the reordered Q: -1 on success, the permuted breakdown row otherwise.
+int64_t or_factor_q(void* hv) {
+  Handle* h = static_cast<Handle*>(hv);
+  try {
+    int64_t r = ic0(h->P.Q, h->permQ, h->LQ);
+    h->qfactored = (r < 0);
+    return r;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return -99;
+  }
 }
 
 // Returns -1 on success, the permuted breakdown row otherwise.
@@ -155,20 +192,32 @@ void or_manufactured_point(double nu, double x, double y, double* out) {
   manufactured_point(nu, x, y, out);
 }
 
-// info[0] outer its, [1] relres estimate, [2] true relres, [3] status
+// info[0] outer its, [1] relres estimate, [2] true relres, [3] status.
+// pressure: PRESSURE_DIAG or PRESSURE_PCG (needs or_factor_q); forced /
+// forced_q replay the inner counts of the velocity / pressure CG.
 int or_minres(void* hv, const double* b, double* x, double tol, double inner_tol, int max_outer,
-              int max_inner, const int32_t* forced, int64_t nforced, double* info) {
+              int max_inner, const int32_t* forced, int64_t nforced, int pressure,
+              const int32_t* forced_q, int64_t nforced_q, double* info) {
   Handle* h = static_cast<Handle*>(hv);
-  if (!h->factored) {
+  if (!h->factored || (pressure == PRESSURE_PCG && !h->qfactored)) {
     g_err = "factor first";
     return -1;
   }
   OR_TRY(Precond M; M.P = &h->P; M.L = &h->L; M.perm = &h->perm; M.inner_tol = inner_tol;
          M.max_inner = max_inner; M.forced = forced; M.nforced = forced ? nforced : 0;
+         M.pressure = pressure; M.LQ = &h->LQ; M.permQ = &h->permQ; M.forced_q = forced_q;
+         M.nforced_q = forced_q ? nforced_q : 0;
          MinresInfo mi; minres(h->P, M, b, x, tol, max_outer, mi);
-         pressure_filter(h->P, x + h->P.n_u); h->counts = M.counts; h->hist = mi.hist;
-         info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
+         pressure_filter(h->P, x + h->P.n_u); h->counts = M.counts; h->qcounts = M.qcounts;
+         h->hist = mi.hist; info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
          info[3] = mi.status; return 0;)
+}
+
+int64_t or_qcounts(void* hv, int32_t* out, int64_t cap) {
+  Handle* h = static_cast<Handle*>(hv);
+  int64_t n = (int64_t)h->qcounts.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) out[i] = h->qcounts[i];
+  return n;
 }
 
 int64_t or_counts(void* hv, int32_t* out, int64_t cap) {
@@ -191,10 +240,21 @@ int or_pcg(void* hv, const double* b, double* x, double inner_tol, int max_inner
          M.max_inner = max_inner; return pcg_ic0(h->P, M, b, x, -1);)
 }
 
-int or_precond(void* hv, const double* r, double* z, double inner_tol, int max_inner) {
+int or_pcg_q(void* hv, const double* b, double* x, double inner_tol, int max_inner) {
+  Handle* h = static_cast<Handle*>(hv);
+  if (!h->qfactored) {
+    g_err = "factor Q first";
+    return -1;
+  }
+  OR_TRY(Precond M; M.P = &h->P; M.LQ = &h->LQ; M.permQ = &h->permQ; M.inner_tol = inner_tol;
+         M.max_inner = max_inner; return pcg_ic0_q(h->P, M, b, x, -1);)
+}
+
+int or_precond(void* hv, const double* r, double* z, double inner_tol, int max_inner, int pressure) {
   Handle* h = static_cast<Handle*>(hv);
   OR_TRY(Precond M; M.P = &h->P; M.L = &h->L; M.perm = &h->perm; M.inner_tol = inner_tol;
-         M.max_inner = max_inner; precond_apply(h->P, M, r, z); return M.counts[0];)
+         M.max_inner = max_inner; M.pressure = pressure; M.LQ = &h->LQ; M.permQ = &h->permQ;
+         precond_apply(h->P, M, r, z); return M.counts[0];)
 }
 
 int or_stokes_apply(void* hv, const double* x, double* y) {

@@ -95,6 +95,9 @@ void manufactured_point(double nu, double x, double y, double out[5]);
 // -------------------------------------------------------------- ordering.cpp
 // perm[new] = old.  kind 0 natural, 1 reverse Cuthill-McKee, 2 multicolour.
 void make_ordering(const Problem& P, int kind, std::vector<int32_t>& perm);
+// The same three orderings of the pressure space, applied to Q before its
+// IC(0) (Sec. 6.4 reorders A and Q separately by reverse Cuthill-McKee).
+void make_pressure_ordering(const Problem& P, int kind, std::vector<int32_t>& perm);
 // Lower-triangular pattern of perm A perm^T (diagonal included, sorted).
 void lower_pattern(const Csr& A, const std::vector<int32_t>& perm, Csr& L);
 // level(i) = 0 without off-diagonal entries, else 1 + max level(k) over
@@ -106,16 +109,27 @@ void level_sets(const Csr& L, std::vector<int32_t>& level, std::vector<int32_t>&
 // success, else the (permuted) row where the pivot was not positive.
 int64_t ic0(const Csr& A, const std::vector<int32_t>& perm, Csr& L);
 
+// Pressure block of the preconditioner (Sec. 5.1): Diag(Q_nu), or Q_nu
+// approximated by an IC(0)-preconditioned CG solve ("IC(0)-PCG(A,Q)",
+// Sec. 6.4) with the same relative tolerance and cap as the velocity block.
+enum PressureBlock { PRESSURE_DIAG = 0, PRESSURE_PCG = 1 };
+
 struct Precond {
   const Problem* P;
-  const Csr* L;                  // IC(0) factor, permuted numbering
+  const Csr* L;                  // IC(0) factor of A_h, permuted numbering
   const std::vector<int32_t>* perm;
   double inner_tol;
   int max_inner;
   const int32_t* forced = nullptr;  // replay: inner counts per application
   int64_t nforced = 0;
+  int pressure = PRESSURE_DIAG;
+  const Csr* LQ = nullptr;       // IC(0) factor of Q (PRESSURE_PCG)
+  const std::vector<int32_t>* permQ = nullptr;
+  const int32_t* forced_q = nullptr;  // replay: pressure CG counts per application
+  int64_t nforced_q = 0;
   // outputs
   std::vector<int32_t> counts;   // inner iterations of each application
+  std::vector<int32_t> qcounts;  // pressure CG iterations of each application
 };
 struct MinresInfo {
   int outer = 0;
@@ -126,6 +140,8 @@ struct MinresInfo {
 void spmv(const Csr& M, const double* x, double* y);
 void stokes_apply(const Problem& P, const double* x, double* y);
 int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced_its);
+// The same CG on the pressure mass matrix Q with its IC(0) factor.
+int pcg_ic0_q(const Problem& P, Precond& M, const double* b, double* x, int forced_its);
 void precond_apply(const Problem& P, Precond& M, const double* r, double* z);
 void minres(const Problem& P, Precond& M, const double* b, double* x, double tol,
             int max_outer, MinresInfo& info);

@@ -122,6 +122,39 @@ static void multicolour(const Problem& P, std::vector<int32_t>& perm) {
                    [&](int32_t a, int32_t b) { return colour[a] < colour[b]; });
 }
 
+// Multicolour ordering of the pressure space: DOF (l_1..l_d) of degree p-1
+// gets colour (l_k mod p for each direction k); two pressure DOFs couple in
+// Q only if |l_k - l'_k| <= p-1 in every direction.
+static void multicolour_pressure(const Problem& P, std::vector<int32_t>& perm) {
+  const int64_t n = P.n_p;
+  std::vector<int64_t> colour(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int a[3] = {0, 0, 0};
+    P.pdecode(i, a);
+    int64_t col = 0;
+    for (int k = 0; k < P.dim; ++k) col = col * P.p + (a[k] % P.p);
+    colour[i] = col;
+  }
+  perm.resize(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+  std::stable_sort(perm.begin(), perm.end(),
+                   [&](int32_t a, int32_t b) { return colour[a] < colour[b]; });
+}
+
+void make_pressure_ordering(const Problem& P, int kind, std::vector<int32_t>& perm) {
+  const int64_t n = P.n_p;
+  if (kind == 0) {
+    perm.resize(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+  } else if (kind == 1) {
+    rcm(P.Q, perm);
+  } else if (kind == 2) {
+    multicolour_pressure(P, perm);
+  } else {
+    throw std::runtime_error("unknown ordering");
+  }
+}
+
 void make_ordering(const Problem& P, int kind, std::vector<int32_t>& perm) {
   const int64_t n = P.n_u;
   if (kind == 0) {

@@ -2,7 +2,8 @@
 // Sec. 5: preconditioned MINRES on the Stokes matrix with the block diagonal
 // preconditioner diag(M_A, M_Q) of eq. general_precond_M, where M_A^{-1} is a
 // relaxed inner conjugate-gradient solve on A_h preconditioned by IC(0)
-// (Sec. 6.4) and M_Q = Diag(Q_nu), Q_nu = Q/(2 nu) (Sec. 5.1).
+// (Sec. 6.4) and M_Q = Diag(Q_nu), Q_nu = Q/(2 nu) (Sec. 5.1), or a CG solve
+// with Q_nu preconditioned by IC(0) of Q (Sec. 6.4, "IC(0)-PCG(A,Q)").
 #include <cmath>
 #include <stdexcept>
 
@@ -88,31 +89,32 @@ static void ic0_solve(const Csr& L, const double* r, double* z, std::vector<doub
   }
 }
 
-static void ic0_apply(const Precond& M, const double* r, double* z) {
-  const int64_t n = M.L->nrows;
-  const std::vector<int32_t>& perm = *M.perm;
+static void ic0_apply(const Csr& L, const std::vector<int32_t>& perm, const double* r, double* z) {
+  const int64_t n = L.nrows;
   std::vector<double> rp(n), zp(n), tmp;
   for (int64_t i = 0; i < n; ++i) rp[i] = r[perm[i]];
-  ic0_solve(*M.L, rp.data(), zp.data(), tmp);
+  ic0_solve(L, rp.data(), zp.data(), tmp);
   for (int64_t i = 0; i < n; ++i) z[perm[i]] = zp[i];
 }
 
-// Inner preconditioned CG on A_h (Sec. 5.1 "PCG(A)", Sec. 6.4 with IC(0)):
-// x_0 = 0; stop when ||r||_2 <= inner_tol ||b||_2 or after max_inner
-// iterations; with forced_its >= 0 exactly forced_its iterations are run.
-// The count is the number of products with A.
-int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced_its) {
-  const int64_t n = P.n_u;
+// Preconditioned CG on the SPD matrix Mat with the IC(0) factor L of
+// perm Mat perm^T (Sec. 5.1 "PCG", Sec. 6.4 with IC(0)): x_0 = 0; stop when
+// ||r||_2 <= tol ||b||_2 or after max_it iterations; with forced_its >= 0
+// exactly forced_its iterations are run.  The count is the number of
+// products with Mat.
+static int pcg(const Csr& Mat, const Csr& L, const std::vector<int32_t>& perm, double tol, int max_it,
+               const double* b, double* x, int forced_its) {
+  const int64_t n = Mat.nrows;
   for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
   const double bnorm = std::sqrt(dot(b, b, n));
   if (bnorm == 0.0 || forced_its == 0) return 0;
   std::vector<double> r(b, b + n), z(n), p(n), q(n);
-  ic0_apply(M, r.data(), z.data());
+  ic0_apply(L, perm, r.data(), z.data());
   p = z;
   double rho = dot(r.data(), z.data(), n);
   int it = 0;
   for (;;) {
-    spmv(P.A, p.data(), q.data());
+    spmv(Mat, p.data(), q.data());
     ++it;
     const double alpha = rho / dot(p.data(), q.data(), n);
     for (int64_t i = 0; i < n; ++i) {
@@ -123,9 +125,9 @@ int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced
       if (it >= forced_its) break;
     } else {
       const double rnorm = std::sqrt(dot(r.data(), r.data(), n));
-      if (rnorm <= M.inner_tol * bnorm || it >= M.max_inner) break;
+      if (rnorm <= tol * bnorm || it >= max_it) break;
     }
-    ic0_apply(M, r.data(), z.data());
+    ic0_apply(L, perm, r.data(), z.data());
     const double rho_new = dot(r.data(), z.data(), n);
     const double beta = rho_new / rho;
     for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
@@ -134,7 +136,20 @@ int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced
   return it;
 }
 
-// z = M^{-1} r with M = diag(M_A, Diag(Q_nu)).
+// Inner CG on A_h (Sec. 5.1 "PCG(A)").
+int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced_its) {
+  return pcg(P.A, *M.L, *M.perm, M.inner_tol, M.max_inner, b, x, forced_its);
+}
+
+// CG on the pressure mass matrix Q (Sec. 6.4, "PCG(Q)").
+int pcg_ic0_q(const Problem& P, Precond& M, const double* b, double* x, int forced_its) {
+  if (!M.LQ || !M.permQ) throw std::runtime_error("pressure CG needs the IC(0) factor of Q");
+  return pcg(P.Q, *M.LQ, *M.permQ, M.inner_tol, M.max_inner, b, x, forced_its);
+}
+
+// z = M^{-1} r with M = diag(M_A, M_Q): M_Q = Diag(Q_nu), or the CG solve
+// with Q_nu = Q / (2 nu), i.e. z_p = 2 nu y with Q y ~= r_p (the relative
+// stopping test is unchanged by the scaling).
 void precond_apply(const Problem& P, Precond& M, const double* r, double* z) {
   int forced = -1;
   const int64_t app = (int64_t)M.counts.size();
@@ -144,6 +159,17 @@ void precond_apply(const Problem& P, Precond& M, const double* r, double* z) {
   }
   int its = pcg_ic0(P, M, r, z, forced);
   M.counts.push_back(its);
+  if (M.pressure == PRESSURE_PCG) {
+    int forced_q = -1;
+    if (M.forced_q) {
+      if (app >= M.nforced_q) throw std::runtime_error("replay: ran out of forced pressure counts");
+      forced_q = M.forced_q[app];
+    }
+    std::vector<double> y(P.n_p);
+    M.qcounts.push_back(pcg_ic0_q(P, M, r + P.n_u, y.data(), forced_q));
+    for (int64_t k = 0; k < P.n_p; ++k) z[P.n_u + k] = 2.0 * P.nu * y[k];
+    return;
+  }
   for (int64_t k = 0; k < P.n_p; ++k) {
     double qkk = P.Q.val[P.Q.find(k, (int32_t)k)];
     z[P.n_u + k] = 2.0 * P.nu * r[P.n_u + k] / qkk;

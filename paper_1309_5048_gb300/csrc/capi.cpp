@@ -191,6 +191,14 @@ int gb_factor_ic0(gb_ctx* h, int64_t* breakdown_row_host) {
   return GB_OK;
 }
 
+// Status of a completed solve call, with the message for gb_last_error.
+static int solve_result(int st) {
+  if (st == GB_ERR_NOT_CONVERGED) set_error("a right-hand side reached max_outer (outputs written)");
+  else if (st == GB_ERR_NONFINITE) set_error("a right-hand side or iterate is not finite");
+  else if (st == GB_ERR_INVALID_ARG) set_error("a right-hand side violates 1^T g_p = 0 (not solved)");
+  return st;
+}
+
 int gb_solve(gb_ctx* h, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts* opts,
              gb_info* info_host) {
   if (!h || !opts) return GB_ERR_INVALID_ARG;
@@ -199,7 +207,7 @@ int gb_solve(gb_ctx* h, const double* rhs_dev, double* x_dev, int k, const gb_so
     StreamOrder order(h->c);
     st2 = solve(h->c, rhs_dev, x_dev, k, *opts, info_host, false);
   });
-  return st != GB_OK ? st : st2;
+  return st != GB_OK ? st : solve_result(st2);
 }
 
 int gb_solve_host(gb_ctx* h, const double* rhs_host, double* x_host, int k, const gb_solve_opts* opts,
@@ -210,7 +218,7 @@ int gb_solve_host(gb_ctx* h, const double* rhs_host, double* x_host, int k, cons
     StreamOrder order(h->c);
     st2 = solve_host(h->c, rhs_host, x_host, k, *opts, info_host);
   });
-  return st != GB_OK ? st : st2;
+  return st != GB_OK ? st : solve_result(st2);
 }
 
 int gb_solve_adjoint(gb_ctx* h, const double* grad_dev, double* lam_dev, int k, const gb_solve_opts* opts,
@@ -221,7 +229,7 @@ int gb_solve_adjoint(gb_ctx* h, const double* grad_dev, double* lam_dev, int k, 
     StreamOrder order(h->c);
     st2 = solve(h->c, grad_dev, lam_dev, k, *opts, info_host, true);
   });
-  return st != GB_OK ? st : st2;
+  return st != GB_OK ? st : solve_result(st2);
 }
 
 int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double* out_host) {

@@ -62,6 +62,8 @@ enum ScalarField {
   S_RHO, S_ALPHA, S_CG_BNORM, S_RNORM, S_CG_ITS, S_CG_ACTIVE, S_CG_TARGET,
   // statistics
   S_INNER_TOTAL, S_INNER_MAX, S_APPS, S_TRUE_RES, S_NONFINITE, S_PMEAN,
+  // right-hand side whose pressure part violates 1^T g_p = 0
+  S_INCONSISTENT,
   S_NFIELDS
 };
 

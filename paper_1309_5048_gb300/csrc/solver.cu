@@ -508,11 +508,15 @@ int collect_info(Ctx& c, int k, gb_info* info) {
     int st = GB_OK;
     if (f(S_STATUS) == 3.0) st = GB_ERR_DEVICE_TIMEOUT;
     else if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
+    else if (f(S_INCONSISTENT) != 0.0) st = GB_ERR_INVALID_ARG;
     else if (f(S_STATUS) != 0.0) st = GB_ERR_NOT_CONVERGED;
     I.status = st;
-    if (st == GB_ERR_DEVICE_TIMEOUT || (st == GB_ERR_NONFINITE && worst != GB_ERR_DEVICE_TIMEOUT) ||
-        (st != GB_OK && worst == GB_OK))
-      worst = st;
+    // severity: device timeout > nonfinite > invalid argument > not converged
+    auto rank = [](int v) {
+      return v == GB_ERR_DEVICE_TIMEOUT ? 4 : v == GB_ERR_NONFINITE ? 3 : v == GB_ERR_INVALID_ARG ? 2
+                                                                     : v == GB_ERR_NOT_CONVERGED ? 1 : 0;
+    };
+    if (rank(st) > rank(worst)) worst = st;
   }
   return worst;
 }

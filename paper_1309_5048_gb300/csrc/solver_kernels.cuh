@@ -101,11 +101,15 @@ __device__ __forceinline__ const float* pick<float>(const double*, const float* 
 
 // ---------------------------------------------------------------- gather --
 // b (internal layout) from rhs [k][n] (natural numbering); zero the MINRES
-// vectors; ||b||^2 and a finiteness check per RHS; scalar initialisation.
+// vectors; ||b||^2, a finiteness check and the consistency condition
+// 1^T g_p = 0 per RHS (K is singular with kernel [0; 1]: B^T 1 = 0 because
+// the pressure B-splines sum to one and the velocity has zero normal trace);
+// scalar initialisation.  A RHS with |1^T g_p| > 1e-10 sqrt(n_p) ||g_p|| is
+// not solved and reports an invalid argument.
 template <int K>
 __global__ void k_gather(Args a, const double* __restrict__ rhs) {
   const int n = a.n_u + a.n_p;
-  double vals[2] = {0.0, 0.0};  // ||b||^2, nonfinite count
+  double vals[4] = {0.0, 0.0, 0.0, 0.0};  // ||b||^2, nonfinite count, 1^T g_p, ||g_p||^2
   const int t = threadIdx.x % K;
   const int stride = (gridDim.x * blockDim.x) / K;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
@@ -122,18 +126,24 @@ __global__ void k_gather(Args a, const double* __restrict__ rhs) {
     a.W1[idx] = 0.0;
     vals[0] += v * v;
     if (!isfinite(v)) vals[1] += 1.0;
+    if (r >= a.n_u) {
+      vals[2] += v;
+      vals[3] += v * v;
+    }
   }
-  block_partials<K, 2>(vals, a.partial);
+  block_partials<K, 4>(vals, a.partial);
   if (last_block(a.counter)) {
-    __shared__ double tot[K * 2];
-    finalize_partials<K, 2>(a.partial, gridDim.x, tot);
+    __shared__ double tot[K * 4];
+    finalize_partials<K, 4>(a.partial, gridDim.x, tot);
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
       for (int f = 0; f < S_NFIELDS; ++f) SF(a, f, s, K) = 0.0;
-      const double bn = sqrt(tot[s * 2 + 0]);
+      const double bn = sqrt(tot[s * 4 + 0]);
       SF(a, S_BNORM, s, K) = bn;
-      SF(a, S_NONFINITE, s, K) = tot[s * 2 + 1] > 0 ? 1.0 : 0.0;
-      const bool live = s < a.k && bn > 0.0 && tot[s * 2 + 1] == 0.0;
+      SF(a, S_NONFINITE, s, K) = tot[s * 4 + 1] > 0 ? 1.0 : 0.0;
+      const bool bad_p = fabs(tot[s * 4 + 2]) > 1e-10 * sqrt((double)a.n_p) * sqrt(tot[s * 4 + 3]);
+      SF(a, S_INCONSISTENT, s, K) = (s < a.k && bad_p) ? 1.0 : 0.0;
+      const bool live = s < a.k && bn > 0.0 && tot[s * 4 + 1] == 0.0 && !bad_p;
       SF(a, S_OUTER_ACTIVE, s, K) = live ? 1.0 : 0.0;
       SF(a, S_C, s, K) = 1.0;
       SF(a, S_C_PREV, s, K) = 1.0;

@@ -338,3 +338,35 @@ def test_full_size_2d_256_replay_parity(oracle_mod, gb):
     x, info = s.solve(rhs, tol=1e-8, inner_tol=1e-2, forced=ir["counts"])
     assert info["outer_its"] == ir["outer"]
     assert rel(x.cpu().numpy(), xr) <= 1e-10
+
+
+def test_pressure_rhs_consistency_check(oracle_mod, gb):
+    """K is singular with kernel [0; 1] (B^T 1 = 0), so a right-hand side is
+    consistent only if 1^T g_p = 0.  A zero-sum pressure part is solved and
+    matches the oracle; a column with a nonzero sum is not solved and reports
+    an invalid argument, while the other columns of the batch are solved."""
+    ref, s = make_pair(oracle_mod, gb, 2, 6, 3)
+    assert ref.factor() < 0
+    s.factor_ic0()
+    b, rhs = _rhs(ref, s, "fourier", seed=4)
+    rng = np.random.default_rng(9)
+    gp = rng.standard_normal(ref.n_p)
+    gp -= gp.mean()
+    b[ref.n_u:] = gp
+    rhs[s.n_u:] = torch.tensor(gp, device="cuda")
+    xr, _ = ref.minres(b, tol=1e-12, inner_tol=1e-4)
+    x, info = s.solve(rhs, tol=1e-12, inner_tol=1e-4)
+    assert info["status"] == 0
+    assert rel(x.cpu().numpy(), xr) <= 1e-8
+    bad = rhs.clone()
+    bad[s.n_u] += 1.0
+    with pytest.raises(gb.GbError) as ei:
+        s.solve(bad)
+    assert ei.value.status == 1
+    pair = torch.stack([rhs, bad])
+    out = torch.full_like(pair, 7.0)
+    with pytest.raises(gb.GbError) as ei:
+        s.solve(pair, out=out, tol=1e-12, inner_tol=1e-4)
+    assert ei.value.status == 1
+    assert rel(out[0].cpu().numpy(), xr) <= 1e-8
+    assert not out[1].any()
