@@ -67,6 +67,16 @@ extern "C" {
 #define GB_PREC_FP64 0
 #define GB_PREC_MIXED 1
 
+/* Pressure block M_Q of the preconditioner (Sec. 5.1, Sec. 6.4).
+ * GB_PRESSURE_DIAG: M_Q = Diag(Q_nu).  GB_PRESSURE_PCG: M_Q^{-1} r_p is a CG
+ * solve with Q_nu = Q / (2 nu) preconditioned by IC(0) of Q in the natural
+ * order ("IC(0)-PCG(A,Q)"), with the same relative tolerance and cap as the
+ * velocity block.  In that order the IC(0) factor of Q is its exact Cholesky
+ * factor (Q is a Kronecker product of banded 1D mass matrices), so the
+ * pressure CG normally stops after one iteration. */
+#define GB_PRESSURE_DIAG 0
+#define GB_PRESSURE_PCG 1
+
 typedef struct gb_ctx gb_ctx;
 
 typedef struct {
@@ -90,6 +100,11 @@ typedef struct {
                        forced_inner_host[i] inner iterations, ignoring
                        inner_tol.  NULL for normal operation. */
   int64_t nforced;  /* length of forced_inner_host */
+  int pressure_block; /* GB_PRESSURE_* */
+  const int32_t* forced_q_host; /* optional replay of the pressure CG counts
+                       (GB_PRESSURE_PCG, k == 1): the i-th application runs
+                       exactly forced_q_host[i] iterations.  NULL otherwise. */
+  int64_t nforced_q; /* length of forced_q_host */
 } gb_solve_opts;
 
 typedef struct {
@@ -99,6 +114,8 @@ typedef struct {
   int inner_its_max;   /* largest inner count of one application */
   double relres_est;   /* |eta| / gamma_1 at exit */
   double relres_true;  /* ||b - K x||_2 / ||b||_2 recomputed at exit */
+  int64_t q_inner_its_total; /* pressure CG iterations (GB_PRESSURE_PCG) */
+  int q_inner_its_max;       /* largest pressure CG count of one application */
   int status;          /* GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_NONFINITE or
                           GB_ERR_INVALID_ARG (inconsistent pressure rhs) */
 } gb_info;
@@ -189,7 +206,8 @@ int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, doubl
 int gb_dnu_noalloc(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
 
 /* y = K x (which = 0), y_u = A_h x_u (which = 1), y_p = B x_u (which = 2),
- * y_u = B^T x_p (which = 3), all in natural numbering, FP64, one vector.
+ * y_u = B^T x_p (which = 3), y_p = Q x_p (which = 4, the pressure mass
+ * matrix), all in natural numbering, FP64, one vector.
  * x_dev / y_dev sizes follow the operator. */
 int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
@@ -228,7 +246,14 @@ int gb_time_kernel(gb_ctx* ctx, int which, int reps, double* ms_host);
  *  what 3: ordering: p0 = int32 perm[new] = old (n_u); p1 = int32 forward
  *          level per row in the ordering's numbering; p2 = int32 backward
  *          level
- *  what 4: Diag(Q) (p2 double [n_p]) and w (p1 double [n_p]) */
+ *  what 4: Diag(Q) (p2 double [n_p]) and w (p1 double [n_p])
+ *  what 5: Q CSR in natural numbering: rowptr int32 [n_p+1], col int32,
+ *          val double [nnz(Q)]
+ *  what 6: the 1D mass matrix Q1 of the degree p-1 B-splines and its
+ *          Cholesky factor L1 (after gb_factor_ic0), as bands of
+ *          (N + p - 1) x p doubles: p0[a*p + o] = Q1[a][a-o],
+ *          p1[a*p + o] = L1[a][a-o] (0 where a < o).  IC(0) of Q in the
+ *          natural order equals L1 x L1 (x L1 in 3D). */
 int gb_export(gb_ctx* ctx, int what, void* p0, void* p1, void* p2);
 
 /* Releases all device and host memory of the context (NULL is allowed). */

@@ -21,6 +21,7 @@ _lib = None
 
 ORDERINGS = {"natural": 0, "rcm": 1, "multicolour": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+PRESSURE_BLOCKS = {"diag": 0, "pcg": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "IC(0) breakdown",
           5: "not converged", 6: "non-finite value", 7: "device wait timed out"}
 GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_IC0_BREAKDOWN = 0, 5, 4
@@ -39,13 +40,14 @@ class gb_problem(C.Structure):
 class gb_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("precision", C.c_int),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("use_graph", C.c_int),
-                ("forced_inner_host", C.c_void_p), ("nforced", C.c_int64)]
+                ("forced_inner_host", C.c_void_p), ("nforced", C.c_int64), ("pressure_block", C.c_int),
+                ("forced_q_host", C.c_void_p), ("nforced_q", C.c_int64)]
 
 
 class gb_info(C.Structure):
     _fields_ = [("outer_its", C.c_int), ("precond_apps", C.c_int), ("inner_its_total", C.c_int64),
                 ("inner_its_max", C.c_int), ("relres_est", C.c_double), ("relres_true", C.c_double),
-                ("status", C.c_int)]
+                ("q_inner_its_total", C.c_int64), ("q_inner_its_max", C.c_int), ("status", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -189,13 +191,20 @@ class Stokes:
     # ------------------------------------------------------------ solves
     @staticmethod
     def options(tol=1e-8, inner_tol=1e-2, precision="fp64", max_outer=5000, max_inner=1000,
-                use_graph=True, forced=None):
-        o = gb_solve_opts(tol, inner_tol, PRECISIONS[precision], max_outer, max_inner, int(use_graph), None, 0)
-        keep = None
+                use_graph=True, forced=None, pressure="diag", forced_q=None):
+        o = gb_solve_opts(tol, inner_tol, PRECISIONS[precision], max_outer, max_inner, int(use_graph), None, 0,
+                          PRESSURE_BLOCKS[pressure], None, 0)
+        keep = []
         if forced is not None:
-            keep = np.ascontiguousarray(forced, dtype=np.int32)
-            o.forced_inner_host = keep.ctypes.data_as(C.c_void_p)
-            o.nforced = keep.size
+            f = np.ascontiguousarray(forced, dtype=np.int32)
+            keep.append(f)
+            o.forced_inner_host = f.ctypes.data_as(C.c_void_p)
+            o.nforced = f.size
+        if forced_q is not None:
+            fq = np.ascontiguousarray(forced_q, dtype=np.int32)
+            keep.append(fq)
+            o.forced_q_host = fq.ctypes.data_as(C.c_void_p)
+            o.nforced_q = fq.size
         return o, keep
 
     def _solve(self, fn, rhs, out=None, allow_not_converged=True, **kw):
@@ -215,7 +224,9 @@ class Stokes:
     def solve(self, rhs, out=None, **kw):
         """Preconditioned MINRES from x0 = 0 for rhs of shape (n,) or (k, n),
         k <= 32.  Options: tol, inner_tol, precision ('fp64'|'mixed'),
-        max_outer, max_inner, use_graph, forced (replay inner counts)."""
+        max_outer, max_inner, use_graph, pressure ('diag': Diag(Q_nu),
+        'pcg': IC(0)-PCG on Q_nu), forced / forced_q (replay the velocity /
+        pressure inner counts)."""
         return self._solve(load_library().gb_solve, rhs, out, **kw)
 
     def solve_adjoint(self, grad, out=None, **kw):
@@ -281,10 +292,11 @@ class Stokes:
         return out
 
     def apply(self, which, x):
-        """which: 'K' (Stokes operator), 'A', 'B', 'Bt' -- natural numbering."""
-        w = {"K": 0, "A": 1, "B": 2, "Bt": 3}[which]
+        """which: 'K' (Stokes operator), 'A', 'B', 'Bt', 'Q' (pressure mass
+        matrix) -- natural numbering."""
+        w = {"K": 0, "A": 1, "B": 2, "Bt": 3, "Q": 4}[which]
         x = self._dev(x)
-        nout = {"K": self.n, "A": self.n_u, "B": self.n_p, "Bt": self.n_u}[which]
+        nout = {"K": self.n, "A": self.n_u, "B": self.n_p, "Bt": self.n_u, "Q": self.n_p}[which]
         y = self.torch.empty(nout, dtype=self.torch.float64, device=self.device)
         _check(load_library().gb_apply(self._h, w, _ptr(x), _ptr(y)))
         return y
@@ -317,6 +329,25 @@ class Stokes:
         _check(load_library().gb_export(self._h, 4, None, w.ctypes.data_as(C.c_void_p),
                                         q.ctypes.data_as(C.c_void_p)))
         return w, q
+
+    def q_csr(self):
+        """Pressure mass matrix Q (natural numbering): (indptr int64, indices, data)."""
+        ptr = np.zeros(self.n_p + 1, np.int32)
+        col = np.zeros(self.nnzQ, np.int32)
+        val = np.zeros(self.nnzQ, np.float64)
+        _check(load_library().gb_export(self._h, 5, ptr.ctypes.data_as(C.c_void_p),
+                                        col.ctypes.data_as(C.c_void_p), val.ctypes.data_as(C.c_void_p)))
+        return ptr.astype(np.int64), col, val
+
+    def q_factor_bands(self):
+        """Bands (m x p) of the 1D mass matrix Q1 and of its Cholesky factor L1:
+        [a, o] = Q1[a, a-o] and L1[a, a-o]; IC(0) of Q = L1 x L1 (x L1)."""
+        m = self.N + self.p - 1
+        q1 = np.zeros(m * self.p)
+        l1 = np.zeros(m * self.p)
+        _check(load_library().gb_export(self._h, 6, q1.ctypes.data_as(C.c_void_p),
+                                        l1.ctypes.data_as(C.c_void_p), None))
+        return q1.reshape(m, self.p), l1.reshape(m, self.p)
 
 
 # Function-style names matching the C ABI.

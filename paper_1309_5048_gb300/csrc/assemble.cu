@@ -363,6 +363,34 @@ __global__ void k_pressure_diag(AsmParams P, int np, double* __restrict__ qdiag,
   }
 }
 
+// Q_kl = prod_m I(p-1, 0, a_m; p-1, 0, b_m) = (phi_l, phi_k) on the pattern of
+// Q (natural numbering, one thread per row), with its FP32 copy.
+__global__ void k_assemble_Q(AsmParams P, int np, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                             double* __restrict__ val, float* __restrict__ val32) {
+  for (int kr = blockIdx.x * blockDim.x + threadIdx.x; kr < np; kr += gridDim.x * blockDim.x) {
+    int a[3] = {0, 0, 0};
+    pdecode_dev(P.S, kr, a);
+    for (int t = ptr[kr]; t < ptr[kr + 1]; ++t) {
+      int b[3] = {0, 0, 0};
+      pdecode_dev(P.S, col[t], b);
+      double q = 1.0;
+      for (int m = 0; m < P.S.dim; ++m) q *= I1(P, 1, 1, 0, 0, a[m], b[m]);
+      val[t] = q;
+      val32[t] = (float)q;
+    }
+  }
+}
+
+// Lower band of the 1D mass matrix Q1 of the m = N + p - 1 degree-(p-1)
+// B-splines: q1[a * p + o] = Q1[a][a - o] for o = 0 .. p-1 (0 where a < o).
+__global__ void k_mass_band(AsmParams P, int m, double* __restrict__ q1) {
+  const int p = P.S.p;
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < m * p; id += gridDim.x * blockDim.x) {
+    const int a = id / p, o = id % p;
+    q1[id] = a >= o ? I1(P, 1, 1, 0, 0, a, a - o) : 0.0;
+  }
+}
+
 // ---- loads -------------------------------------------------------------
 // S[m][k][s][a] = int_0^1 sin(pi kappa_{m,k} x) B^{q_s}_a(x) dx, Gauss p+3.
 __global__ void k_fourier_1d(int N, int p, int dim, int nmodes, const int32_t* __restrict__ kappa,
@@ -501,9 +529,15 @@ void assemble(Ctx& c, double nu, double cpen) {
   sell_refill(c, c.sA, c.A_val.p);
   k_pressure_diag<<<grid_for(c.n_p, 256), 256, 0, c.stream>>>(P, (int)c.n_p, c.Qdiag.p, c.wmean.p);
   GBS_CUDA(cudaGetLastError());
+  k_assemble_Q<<<grid_for(c.n_p, 256), 256, 0, c.stream>>>(P, (int)c.n_p, c.Q_ptr.p, c.Q_col.p, c.Q_val.p,
+                                                            c.Q_val32.p);
+  GBS_CUDA(cudaGetLastError());
+  k_mass_band<<<grid_for((int64_t)(c.N + c.p - 1) * c.p, 256), 256, 0, c.stream>>>(P, c.N + c.p - 1, c.q1.p);
+  GBS_CUDA(cudaGetLastError());
   GBS_CUDA(cudaStreamSynchronize(c.stream));
   c.assembled = true;
   c.factored = false;
+  c.q_factored = false;
   c.ws.graph_valid = false;
 }
 

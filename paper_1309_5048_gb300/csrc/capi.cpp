@@ -366,6 +366,17 @@ int gb_export(gb_ctx* h, int what, void* p0, void* p1, void* p2) {
       if (p1) dl(p1, c.wmean.p, sizeof(double) * c.n_p);
       if (p2) dl(p2, c.Qdiag.p, sizeof(double) * c.n_p);
       cuda_check(cudaStreamSynchronize(c.stream), "export sync");
+    } else if (what == 5) {
+      if (p0) dl(p0, c.Q_ptr.p, sizeof(int32_t) * (c.n_p + 1));
+      if (p1) dl(p1, c.Q_col.p, sizeof(int32_t) * c.nnzQ);
+      if (p2) dl(p2, c.Q_val.p, sizeof(double) * c.nnzQ);
+      cuda_check(cudaStreamSynchronize(c.stream), "export sync");
+    } else if (what == 6) {
+      if (!c.q_factored) fail(GB_ERR_INVALID_ARG, "factor_ic0 must succeed before exporting the factor of Q");
+      const size_t band = (size_t)(c.N + c.p - 1) * c.p;
+      if (p0) dl(p0, c.q1.p, sizeof(double) * band);
+      if (p1) dl(p1, c.l1.p, sizeof(double) * band);
+      cuda_check(cudaStreamSynchronize(c.stream), "export sync");
     } else {
       fail(GB_ERR_INVALID_ARG, "unknown export");
     }

@@ -97,6 +97,41 @@ void sell_refill(Ctx& c, Sell& S, const double* csr_val) {
   GBS_CUDA(cudaGetLastError());
 }
 
+// IC(0) of the pressure mass matrix in the natural order (Sec. 6.4,
+// "IC(0)-PCG(A,Q)").  Q = Q1 x Q1 [x Q1] with Q1 banded (half-bandwidth
+// p - 1), so the exact Cholesky factor L1 x L1 [x L1] lies inside the lower
+// pattern of Q and IC(0) reproduces it; only the band of L1 is formed:
+//   L1[a][b] = (Q1[a][b] - sum_{c<b} L1[a][c] L1[b][c]) / L1[b][b]   (b < a),
+//   L1[a][a] = sqrt(Q1[a][a] - sum_{c<a} L1[a][c]^2).
+// One thread (m p^2 operations); *bad receives the first non-positive pivot.
+__global__ void k_band_cholesky(int m, int p, const double* __restrict__ q1, double* __restrict__ l1,
+                                float* __restrict__ l1_32, int* __restrict__ bad) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int a = 0; a < m; ++a) {
+    for (int o = p - 1; o >= 1; --o) {  // columns b = a - o in ascending order
+      const int b = a - o;
+      if (b < 0) {
+        l1[a * p + o] = 0.0;
+        continue;
+      }
+      double s = q1[a * p + o];
+      for (int cc = max(a - p + 1, 0); cc < b; ++cc) s -= l1[a * p + (a - cc)] * l1[b * p + (b - cc)];
+      l1[a * p + o] = s / l1[b * p];
+    }
+    double d = q1[a * p];
+    for (int cc = max(a - p + 1, 0); cc < a; ++cc) {
+      const double v = l1[a * p + (a - cc)];
+      d -= v * v;
+    }
+    if (!(d > 0.0)) {
+      *bad = a;
+      return;
+    }
+    l1[a * p] = sqrt(d);
+  }
+  for (int i = 0; i < m * p; ++i) l1_32[i] = (float)l1[i];
+}
+
 int64_t factor_ic0(Ctx& c) {
   if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble before factor_ic0");
   const int n = (int)c.n_u;
@@ -118,9 +153,14 @@ int64_t factor_ic0(Ctx& c) {
   GBS_CUDA(cudaGetLastError());
   sell_refill(c, c.sL, c.L_val.p);
   sell_refill(c, c.sU, c.U_val.p);
-  int bad = 0;
+  GBS_CUDA(cudaMemcpyAsync(c.status_d.p + 1, &init, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  k_band_cholesky<<<1, 32, 0, c.stream>>>(c.N + c.p - 1, c.p, c.q1.p, c.l1.p, c.l1_32.p, c.status_d.p + 1);
+  GBS_CUDA(cudaGetLastError());
+  int bad = 0, bad_q = 0;
   GBS_CUDA(cudaMemcpyAsync(&bad, c.status_d.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaMemcpyAsync(&bad_q, c.status_d.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));
+  c.q_factored = (bad_q == INT32_MAX);
   c.ws.graph_valid = false;
   if (bad != INT32_MAX) {
     c.factored = false;

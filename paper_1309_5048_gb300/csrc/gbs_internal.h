@@ -64,6 +64,8 @@ enum ScalarField {
   S_INNER_TOTAL, S_INNER_MAX, S_APPS, S_TRUE_RES, S_NONFINITE, S_PMEAN,
   // right-hand side whose pressure part violates 1^T g_p = 0
   S_INCONSISTENT,
+  // pressure-block CG on Q (IC(0)-PCG pressure block)
+  S_Q_RHO, S_Q_ALPHA, S_Q_BNORM, S_Q_RNORM, S_Q_ITS, S_Q_ACTIVE, S_Q_TARGET, S_Q_TOTAL, S_Q_MAX,
   S_NFIELDS
 };
 
@@ -118,9 +120,19 @@ struct Workspace {
   void* cg_y = nullptr;
   void* cg_p = nullptr;
   void* cg_q = nullptr;
+  // pressure-block CG on Q (element type T, [n_p][K])
+  void* qcg_x = nullptr;
+  void* qcg_r = nullptr;
+  void* qcg_z = nullptr;
+  void* qcg_p = nullptr;
+  void* qcg_q = nullptr;
+  int32_t* forced_q = nullptr;  // device replay counts of the pressure CG
+  int64_t nforced_q = 0;
+  size_t forced_q_cap = 0;
   double* S = nullptr;          // scalars [S_NFIELDS][K]
   double* S_host = nullptr;     // pinned mirror
-  int* flag = nullptr;          // device: [0] any outer active, [1] any inner active
+  int* flag = nullptr;          // device: [0] any outer active, [1] any inner active,
+                                // [2] MINRES step j, [3] any pressure CG active
   int* flag_host = nullptr;     // pinned
   int32_t* forced = nullptr;    // device replay counts
   int64_t nforced = 0;
@@ -172,6 +184,19 @@ struct Ctx {
   DevBuf<double> B_val, Bt_val;
   DevBuf<double> Qdiag, wmean;
   DevBuf<double> tab1d;  // 1D integral tables (assembly)
+  // Pressure mass matrix Q, natural numbering, for the IC(0)-PCG pressure
+  // block.  Q is the Kronecker product of the 1D mass matrix Q1 of the
+  // degree p-1 B-splines (m = N + p - 1 functions, half-bandwidth p - 1) over
+  // the directions; in the natural (lexicographic) order the exact Cholesky
+  // factor L1 x L1 [x L1] lies inside the lower pattern of Q, so IC(0) of Q
+  // is that factor, kept as the band of L1: l1[a * p + o] = L1[a][a - o].
+  DevBuf<int32_t> Q_ptr, Q_col;
+  DevBuf<double> Q_val;
+  DevBuf<float> Q_val32;
+  DevBuf<double> q1;   // band of Q1, same layout as l1
+  DevBuf<double> l1;
+  DevBuf<float> l1_32;
+  bool q_factored = false;
   Sell sA, sL, sU;                 // SELL-32 copies of A, L, U
   std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
   Staged tL, tU;                   // staged-sweep partitions of L and U = L^T

@@ -526,6 +526,36 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
     c.nnzQ = 1;
     for (int k = 0; k < nb.dim; ++k) c.nnzQ *= per;
   }
+  // pattern of Q (natural pressure numbering, ascending columns): pressure
+  // functions k and l couple iff |a_d - b_d| <= p - 1 in every direction
+  if (c.nnzQ >= INT32_MAX) fail(GB_ERR_INVALID_ARG, "Q exceeds 32-bit indexing");
+  std::vector<int32_t> Qptr(np + 1, 0), Qcol(c.nnzQ);
+  {
+    const int m = nb.N + nb.p - 1, w = nb.p - 1;
+    auto row_len = [&](int64_t k) {
+      int a[3] = {0, 0, 0};
+      nb.pdecode(k, a);
+      int64_t len = 1;
+      for (int d = 0; d < nb.dim; ++d) len *= std::min(m - 1, a[d] + w) - std::max(0, a[d] - w) + 1;
+      return len;
+    };
+    for (int64_t k = 0; k < np; ++k) Qptr[k + 1] = Qptr[k] + (int32_t)row_len(k);
+    parallel_ranges(np, [&](int64_t lo, int64_t hi) {
+      for (int64_t k = lo; k < hi; ++k) {
+        int a[3] = {0, 0, 0}, l[3] = {0, 0, 0}, h[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+        nb.pdecode(k, a);
+        for (int d = 0; d < nb.dim; ++d) {
+          l[d] = std::max(0, a[d] - w);
+          h[d] = std::min(m - 1, a[d] + w);
+        }
+        int32_t t = Qptr[k];
+        for (b[0] = l[0]; b[0] <= h[0]; ++b[0])
+          for (b[1] = (nb.dim > 1 ? l[1] : 0); b[1] <= (nb.dim > 1 ? h[1] : 0); ++b[1])
+            for (b[2] = (nb.dim > 2 ? l[2] : 0); b[2] <= (nb.dim > 2 ? h[2] : 0); ++b[2])
+              Qcol[t++] = (int32_t)nb.pindex(b);
+      }
+    });
+  }
 
   // ---- upload
   cudaStream_t s = c.stream;
@@ -558,6 +588,16 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   c.Bt_val.alloc(c.nnzB);
   c.Qdiag.alloc(np);
   c.wmean.alloc(np);
+  c.Q_ptr.upload(Qptr.data(), np + 1, s);
+  c.Q_col.upload(Qcol.data(), c.nnzQ, s);
+  c.Q_val.alloc(c.nnzQ);
+  c.Q_val32.alloc(c.nnzQ);
+  {
+    const size_t band = (size_t)(nb.N + nb.p - 1) * nb.p;
+    c.q1.alloc(band);
+    c.l1.alloc(band);
+    c.l1_32.alloc(band);
+  }
   build_sell(c.hA_ptr, c.hA_col, c.lev_ptr, c.lev_slice, c.sA, s);
   build_sell(Lptr, Lcol, c.lev_ptr, c.lev_slice, c.sL, s);
   build_sell(Uptr, Ucol, c.lev_ptr, c.lev_slice, c.sU, s);
@@ -573,7 +613,7 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   GBS_CUDA(cudaStreamSynchronize(s));
   c.device_bytes = (size_t)(n + 1) * 4 * 4 + (size_t)c.nnzA * (4 + 8 + 4) + n * 4 * 3 +
                    Lcol.size() * (4 + 8 + 4) + Ucol.size() * (4 + 4 + 8 + 4) + n * 8 * 3 +
-                   (size_t)c.nnzB * (4 * 3 + 8 * 2) + np * 16;
+                   (size_t)c.nnzB * (4 * 3 + 8 * 2) + np * 16 + (size_t)c.nnzQ * (4 + 8 + 4) + np * 4;
 }
 
 }  // namespace gbs

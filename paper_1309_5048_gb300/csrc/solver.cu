@@ -55,6 +55,12 @@ void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
     w.cg_y = dmalloc(cb);
     w.cg_p = dmalloc(cb);
     w.cg_q = dmalloc(cb);
+    const size_t qb = (size_t)c.n_p * K * esz;
+    w.qcg_x = dmalloc(qb);
+    w.qcg_r = dmalloc(qb);
+    w.qcg_z = dmalloc(qb);
+    w.qcg_p = dmalloc(qb);
+    w.qcg_q = dmalloc(qb);
     w.S = (double*)dmalloc(sizeof(double) * S_NFIELDS * K);
     GBS_CUDA(cudaMallocHost((void**)&w.S_host, sizeof(double) * S_NFIELDS * K));
     w.flag = (int*)dmalloc(sizeof(int) * 8);
@@ -146,7 +152,25 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.sA = view(c.sA);
   a.sL = view(c.sL);
   a.sU = view(c.sU);
+  a.dim = c.dim;
+  a.qm = c.N + c.p - 1;
+  a.qp = c.p;
+  a.Q_ptr = c.Q_ptr.p;
+  a.Q_col = c.Q_col.p;
+  a.Q_val = c.Q_val.p;
+  a.Q_val32 = c.Q_val32.p;
+  a.l1 = c.l1.p;
+  a.l1_32 = c.l1_32.p;
+  a.qcg_x = w.qcg_x;
+  a.qcg_r = w.qcg_r;
+  a.qcg_z = w.qcg_z;
+  a.qcg_p = w.qcg_p;
+  a.qcg_q = w.qcg_q;
+  a.pressure_block = GB_PRESSURE_DIAG;
   if (o) {
+    a.pressure_block = o->pressure_block;
+    a.forced_q = o->forced_q_host ? w.forced_q : nullptr;
+    a.nforced_q = o->forced_q_host ? (int)o->nforced_q : 0;
     a.tol = o->tol;
     a.inner_tol = o->inner_tol;
     a.max_outer = o->max_outer;
@@ -298,6 +322,33 @@ struct Run {
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 0);
     k_cg_pupdate<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
+  // Pressure-block CG on Q (GB_PRESSURE_PCG): the IC(0) application is one
+  // pass of banded line solves per direction, alternating between the
+  // z and q buffers so that the last pass lands in z.
+  bool pcg_q() const { return a.pressure_block == GB_PRESSURE_PCG; }
+  void q_lines() {
+    const int64_t threads = (int64_t)c.n_p / (c.N + c.p - 1) * K;
+    const int grid = (int)((threads + 127) / 128);
+    const T* src = (const T*)a.qcg_r;
+    for (int axis = 0; axis < c.dim; ++axis) {
+      T* dst = (T*)(((c.dim - 1 - axis) % 2 == 0) ? a.qcg_z : a.qcg_q);
+      k_q_lines<K, T><<<grid, 128, 0, s>>>(a, axis, src, dst);
+      src = dst;
+    }
+  }
+  void qcg_prologue() {
+    q_lines();
+    k_cg_rho<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a, 1);
+  }
+  void qcg_head() {
+    k_cg_spmv<K, T, 1><<<grid_cap(c.n_p * G), kBlock, 0, s>>>(a);
+    k_cg_axpy<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a);
+  }
+  void qcg_tail() {
+    q_lines();
+    k_cg_rho<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a, 0);
+    k_cg_pupdate<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a);
+  }
   void finish(double* out) {
     k_residual<K><<<grid_cap(n() * G), kBlock, 0, s>>>(a);
     k_scatter<K><<<grid_cap(n() * K), kBlock, 0, s>>>(a, out);
@@ -313,6 +364,13 @@ struct Run {
       cg_head();
       if (!read_flag(1)) break;
       cg_tail();
+    }
+    if (!pcg_q()) return;
+    qcg_prologue();
+    for (;;) {
+      qcg_head();
+      if (!read_flag(3)) break;
+      qcg_tail();
     }
   }
   void run_host(const double* rhs, double* out) {
@@ -362,19 +420,25 @@ struct Run {
   cudaGraphExec_t build_graph(const double* rhs, double* out) {
     cudaGraph_t g;
     GBS_CUDA(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h_out, h_in0, h_in;
+    cudaGraphConditionalHandle h_out, h_in0, h_in, h_q0 = 0, h_q = 0;
     GBS_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 0, 0));
     GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in0, g, 0, 0));
+    if (pcg_q()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_q0, g, 0, 0));
     const Args base = a;
     a.use_handles = 1;
     a.h_outer = h_out;
     a.h_inner = h_in0;
-    cudaGraph_t body0 = nullptr, bodyO = nullptr, bodyI = nullptr;
+    a.h_qinner = h_q0;
+    cudaGraph_t body0 = nullptr, bodyO = nullptr, bodyI = nullptr, bodyQ0 = nullptr, bodyQ = nullptr;
     capture_into(g, [&] {
       gather(rhs);
       lanczos();
       cg_prologue();
       body0 = add_while(h_in0);
+      if (pcg_q()) {
+        qcg_prologue();
+        bodyQ0 = add_while(h_q0);
+      }
       gamma();
       bodyO = add_while(h_out);
       finish(out);
@@ -383,13 +447,24 @@ struct Run {
       cg_head();
       cg_tail();
     });
+    if (pcg_q())
+      capture_into(bodyQ0, [&] {
+        qcg_head();
+        qcg_tail();
+      });
     GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in, bodyO, 0, 0));
+    if (pcg_q()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_q, bodyO, 0, 0));
     a.h_inner = h_in;
+    a.h_qinner = h_q;
     capture_into(bodyO, [&] {
       stokes();
       lanczos();
       cg_prologue();
       bodyI = add_while(h_in);
+      if (pcg_q()) {
+        qcg_prologue();
+        bodyQ = add_while(h_q);
+      }
       gamma();
       update();
     });
@@ -397,6 +472,11 @@ struct Run {
       cg_head();
       cg_tail();
     });
+    if (pcg_q())
+      capture_into(bodyQ, [&] {
+        qcg_head();
+        qcg_tail();
+      });
     a = base;
     cudaGraphExec_t exec = nullptr;
     GBS_CUDA(cudaGraphInstantiate(&exec, g, 0));
@@ -477,7 +557,8 @@ void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solv
   }
   std::vector<double> key = {(double)(uintptr_t)rhs, (double)(uintptr_t)out, (double)k, o.tol, o.inner_tol,
                              (double)o.max_outer, (double)o.max_inner, (double)K, (double)o.precision,
-                             (double)a.nforced, c.nu, (double)run.vspmv, (double)run.vtrsv};
+                             (double)a.nforced, c.nu, (double)run.vspmv, (double)run.vtrsv,
+                             (double)o.pressure_block, (double)a.nforced_q};
   if (!w.graph_valid || w.graph_key != key) {
     if (w.graph) {
       cudaGraphExecDestroy(w.graph);
@@ -505,6 +586,8 @@ int collect_info(Ctx& c, int k, gb_info* info) {
     I.inner_its_max = (int)f(S_INNER_MAX);
     I.relres_est = f(S_RELRES);
     I.relres_true = f(S_TRUE_RES);
+    I.q_inner_its_total = (int64_t)f(S_Q_TOTAL);
+    I.q_inner_its_max = (int)f(S_Q_MAX);
     int st = GB_OK;
     if (f(S_STATUS) == 3.0) st = GB_ERR_DEVICE_TIMEOUT;
     else if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
@@ -587,7 +670,8 @@ void release_workspace(Ctx& c) {
   if (w.graph) cudaGraphExecDestroy(w.graph);
   void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
                   w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
-                  w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out};
+                  w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out, w.qcg_x, w.qcg_r, w.qcg_z,
+                  w.qcg_p, w.qcg_q, w.forced_q};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w.S_host) cudaFreeHost(w.S_host);
@@ -605,9 +689,26 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
   if (o.precision != GB_PREC_FP64 && o.precision != GB_PREC_MIXED) fail(GB_ERR_INVALID_ARG, "bad precision");
   if (o.forced_inner_host && (k != 1 || o.nforced < 1 || o.nforced > (1 << 24)))
     fail(GB_ERR_INVALID_ARG, "replay mode needs k == 1 and 1 <= nforced <= 2^24");
+  if (o.pressure_block != GB_PRESSURE_DIAG && o.pressure_block != GB_PRESSURE_PCG)
+    fail(GB_ERR_INVALID_ARG, "bad pressure block");
+  if (o.forced_q_host && (o.pressure_block != GB_PRESSURE_PCG || k != 1 || o.nforced_q < 1 ||
+                          o.nforced_q > (1 << 24)))
+    fail(GB_ERR_INVALID_ARG, "pressure replay needs the PCG pressure block, k == 1, 1 <= nforced_q <= 2^24");
+  if (o.pressure_block == GB_PRESSURE_PCG && !c.q_factored)
+    fail(GB_ERR_IC0_BREAKDOWN, "IC(0) of the pressure mass matrix failed");
   const int K = (k == 1) ? 1 : (k <= 8 ? 8 : 32);
   ensure_workspace(c, K, o.precision, k);
   Workspace& w = c.ws;
+  if (o.forced_q_host) {
+    if ((size_t)o.nforced_q > w.forced_q_cap) {
+      if (w.forced_q) cudaFree(w.forced_q);
+      w.forced_q = (int32_t*)dmalloc(sizeof(int32_t) * o.nforced_q);
+      w.forced_q_cap = o.nforced_q;
+      w.graph_valid = false;
+    }
+    GBS_CUDA(cudaMemcpyAsync(w.forced_q, o.forced_q_host, sizeof(int32_t) * o.nforced_q,
+                             cudaMemcpyHostToDevice, c.stream));
+  }
   if (o.forced_inner_host) {
     if ((size_t)o.nforced > w.forced_cap) {
       if (w.forced) cudaFree(w.forced);
@@ -657,9 +758,9 @@ int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_s
 
 void apply_operator(Ctx& c, int which, const double* x, double* y) {
   if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble first");
-  if (which < 0 || which > 3 || !x || !y) fail(GB_ERR_INVALID_ARG, "bad operator request");
+  if (which < 0 || which > 4 || !x || !y) fail(GB_ERR_INVALID_ARG, "bad operator request");
   Args a = make_args(c, nullptr, 1);
-  const int64_t rows = which == 0 ? c.n_u + c.n_p : (which == 2 ? c.n_p : c.n_u);
+  const int64_t rows = which == 0 ? c.n_u + c.n_p : ((which == 2 || which == 4) ? c.n_p : c.n_u);
   k_apply_natural<<<grid_cap(rows * 8), kBlock, 0, c.stream>>>(a, which, x, y);
   GBS_CUDA(cudaGetLastError());
   GBS_CUDA(cudaStreamSynchronize(c.stream));

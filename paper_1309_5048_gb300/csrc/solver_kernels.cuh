@@ -68,6 +68,47 @@ struct Args {
   cudaGraphConditionalHandle h_outer, h_inner;
   int use_handles;
   SellView sA, sL, sU;  // SELL-32 copies used by the single-RHS variants
+  // pressure block: GB_PRESSURE_DIAG or GB_PRESSURE_PCG (CG on Q with the
+  // exact IC(0) factor L1 x L1 [x L1] of Q, natural numbering)
+  int pressure_block;
+  int dim, qm, qp;  // pressure functions per direction m = N + p - 1; band p of L1
+  const int32_t *Q_ptr, *Q_col;
+  const double* Q_val;
+  const float* Q_val32;
+  const double* l1;
+  const float* l1_32;
+  void *qcg_x, *qcg_r, *qcg_z, *qcg_p, *qcg_q;
+  const int32_t* forced_q;
+  int nforced_q;
+  cudaGraphConditionalHandle h_qinner;
+};
+
+// The two inner CG solves: SYS 0 on A_h (velocity block, Sec. 5.1 "PCG(A)"),
+// SYS 1 on Q (pressure block, Sec. 6.4 "PCG(Q)"): scalar fields, vectors,
+// matrix, replay counts and loop control of each.
+template <int SYS>
+struct CgSys {
+  static constexpr int RHO = SYS ? S_Q_RHO : S_RHO;
+  static constexpr int ALPHA = SYS ? S_Q_ALPHA : S_ALPHA;
+  static constexpr int BNORM = SYS ? S_Q_BNORM : S_CG_BNORM;
+  static constexpr int RNORM = SYS ? S_Q_RNORM : S_RNORM;
+  static constexpr int ITS = SYS ? S_Q_ITS : S_CG_ITS;
+  static constexpr int ACTIVE = SYS ? S_Q_ACTIVE : S_CG_ACTIVE;
+  static constexpr int TARGET = SYS ? S_Q_TARGET : S_CG_TARGET;
+  static constexpr int TOTAL = SYS ? S_Q_TOTAL : S_INNER_TOTAL;
+  static constexpr int MAX = SYS ? S_Q_MAX : S_INNER_MAX;
+  static constexpr int FLAG = SYS ? 3 : 1;  // index in Args::flag of "any active"
+  __device__ static int n(const Args& a) { return SYS ? a.n_p : a.n_u; }
+  __device__ static void* x(const Args& a) { return SYS ? a.qcg_x : a.cg_x; }
+  __device__ static void* r(const Args& a) { return SYS ? a.qcg_r : a.cg_r; }
+  __device__ static void* z(const Args& a) { return SYS ? a.qcg_z : a.cg_z; }
+  __device__ static void* p(const Args& a) { return SYS ? a.qcg_p : a.cg_p; }
+  __device__ static void* q(const Args& a) { return SYS ? a.qcg_q : a.cg_q; }
+  __device__ static const int32_t* ptr(const Args& a) { return SYS ? a.Q_ptr : a.A_ptr; }
+  __device__ static const int32_t* col(const Args& a) { return SYS ? a.Q_col : a.A_col; }
+  __device__ static const double* val(const Args& a) { return SYS ? a.Q_val : a.A_val; }
+  __device__ static const float* val32(const Args& a) { return SYS ? a.Q_val32 : a.A_val32; }
+  __device__ static cudaGraphConditionalHandle handle(const Args& a) { return SYS ? a.h_qinner : a.h_inner; }
 };
 
 template <int K>
@@ -217,9 +258,11 @@ __global__ void k_stokes_apply(Args a) {
 
 // ----------------------------------------------------------- Lanczos -----
 // v_{j+1} = q - (delta_j/gamma_j) v_j - (gamma_j/gamma_{j-1}) v_{j-1}
-// (j = 0: v_1 = b).  The pressure block of z_{j+1} = M^{-1} v_{j+1} is
-// 2 nu v_p / diag(Q); the velocity block starts the inner CG with b = r =
-// v_{j+1,u}, x = 0.  Epilogue: ||b_u|| and the inner CG state per RHS.
+// (j = 0: v_1 = b).  The velocity block of z_{j+1} = M^{-1} v_{j+1} starts
+// the inner CG with b = r = v_{j+1,u}, x = 0.  The pressure block is
+// 2 nu v_p / diag(Q) (Diag(Q_nu)), or starts the pressure CG on Q with
+// b = r = v_{j+1,p}, x = 0 (IC(0)-PCG block; z_p = 2 nu x is taken in
+// k_gamma).  Epilogue: ||b|| and the CG state of each block per RHS.
 template <int K, class T>
 __global__ void k_lanczos(Args a) {
   const int j = *a.jcur;
@@ -230,6 +273,9 @@ __global__ void k_lanczos(Args a) {
   double* __restrict__ zn = Zbuf(a, j + 1);
   T* __restrict__ r_cg = (T*)a.cg_r;
   T* __restrict__ x_cg = (T*)a.cg_x;
+  T* __restrict__ r_q = (T*)a.qcg_r;
+  T* __restrict__ x_q = (T*)a.qcg_x;
+  const bool pcg_q = a.pressure_block == GB_PRESSURE_PCG;
   const int t = threadIdx.x % K;
   const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
   double c1 = 0.0, c2 = 0.0;
@@ -238,7 +284,7 @@ __global__ void k_lanczos(Args a) {
     c1 = SF(a, S_DELTA, t, K) / gm;
     c2 = gm / SF(a, S_GAMMA_PREV, t, K);
   }
-  double vals[1] = {0.0};
+  double vals[2] = {0.0, 0.0};  // ||v_u||^2, ||v_p||^2
   const int stride = (gridDim.x * blockDim.x) / K;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
     if (!live) continue;
@@ -249,45 +295,66 @@ __global__ void k_lanczos(Args a) {
       r_cg[idx] = (T)v;
       x_cg[idx] = (T)0;
       vals[0] += v * v;
+    } else if (pcg_q) {
+      const size_t iq = (size_t)(r - a.n_u) * K + t;
+      r_q[iq] = (T)v;
+      x_q[iq] = (T)0;
+      vals[1] += v * v;
     } else {
       zn[idx] = 2.0 * a.nu * v / a.Qdiag[r - a.n_u];
     }
   }
-  block_partials<K, 1>(vals, a.partial);
+  block_partials<K, 2>(vals, a.partial);
   if (last_block(a.counter)) {
-    __shared__ double tot[K];
-    finalize_partials<K, 1>(a.partial, gridDim.x, tot);
-    int any = 0;
+    __shared__ double tot[K * 2];
+    finalize_partials<K, 2>(a.partial, gridDim.x, tot);
+    int any = 0, anyq = 0;
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
       SF(a, S_CG_ACTIVE, s, K) = 0.0;
+      SF(a, S_Q_ACTIVE, s, K) = 0.0;
       if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
-        const double bn = sqrt(tot[s]);
+        const int app = (int)SF(a, S_APPS, s, K);
+        const double bn = sqrt(tot[s * 2 + 0]);
         SF(a, S_CG_BNORM, s, K) = bn;
         SF(a, S_CG_ITS, s, K) = 0.0;
         double target = -1.0;
-        if (a.forced) {
-          const int app = (int)SF(a, S_APPS, s, K);
-          target = app < a.nforced ? (double)a.forced[app] : 0.0;
-        }
+        if (a.forced) target = app < a.nforced ? (double)a.forced[app] : 0.0;
         SF(a, S_CG_TARGET, s, K) = target;
         SF(a, S_APPS, s, K) += 1.0;
         const bool act = bn > 0.0 && target != 0.0;
         SF(a, S_CG_ACTIVE, s, K) = act ? 1.0 : 0.0;
         any = act;
+        if (pcg_q) {
+          const double bq = sqrt(tot[s * 2 + 1]);
+          SF(a, S_Q_BNORM, s, K) = bq;
+          SF(a, S_Q_ITS, s, K) = 0.0;
+          double tq = -1.0;
+          if (a.forced_q) tq = app < a.nforced_q ? (double)a.forced_q[app] : 0.0;
+          SF(a, S_Q_TARGET, s, K) = tq;
+          const bool actq = bq > 0.0 && tq != 0.0;
+          SF(a, S_Q_ACTIVE, s, K) = actq ? 1.0 : 0.0;
+          anyq = actq;
+        }
       }
     }
     any = __syncthreads_or(any);
+    anyq = __syncthreads_or(anyq);
     if (threadIdx.x == 0) {
       a.flag[1] = any;
-      if (a.use_handles) cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+      a.flag[3] = anyq;
+      if (a.use_handles) {
+        cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+        if (pcg_q) cudaGraphSetConditional(a.h_qinner, anyq ? 1u : 0u);
+      }
       *a.counter = 0;
     }
   }
 }
 
 // ---------------------------------------------------------- gamma/Givens --
-// z_{j+1,u} = x_cg (the inner CG result); gamma_{j+1}^2 = z_{j+1}^T v_{j+1}.
+// z_{j+1,u} = x_cg (the inner CG result), z_{j+1,p} = 2 nu x_q with the
+// IC(0)-PCG pressure block; gamma_{j+1}^2 = z_{j+1}^T v_{j+1}.
 // j = 0: initial recurrence values.  j >= 1: Givens rotation of the new
 // column of the tridiagonal matrix, coefficient of the x update, new eta and
 // the convergence test |eta| / gamma_1 <= tol.
@@ -308,6 +375,9 @@ __global__ void k_gamma(Args a) {
     double z;
     if (r < a.n_u) {
       z = (double)x_cg[idx];
+      zn[idx] = z;
+    } else if (a.pressure_block == GB_PRESSURE_PCG) {
+      z = 2.0 * a.nu * (double)((const T*)a.qcg_x)[(size_t)(r - a.n_u) * K + t];
       zn[idx] = z;
     } else {
       z = zn[idx];
@@ -437,31 +507,35 @@ __global__ void k_update(Args a) {
 }
 
 // ------------------------------------------------------------- inner CG --
-// q = A p and p^T q; epilogue alpha = rho / p^T q.
-template <int K, class T>
+// q = A p (SYS 0) or q = Q p (SYS 1) and p^T q; epilogue alpha = rho / p^T q.
+template <int K, class T, int SYS = 0>
 __global__ void k_cg_spmv(Args a) {
   using M = Map<K>;
-  const T* __restrict__ val = pick<T>(a.A_val, a.A_val32);
-  const T* __restrict__ p = (const T*)a.cg_p;
-  T* __restrict__ q = (T*)a.cg_q;
+  using C = CgSys<SYS>;
+  const T* __restrict__ val = pick<T>(C::val(a), C::val32(a));
+  const int32_t* __restrict__ mptr = C::ptr(a);
+  const int32_t* __restrict__ mcol = C::col(a);
+  const int nrows = C::n(a);
+  const T* __restrict__ p = (const T*)C::p(a);
+  T* __restrict__ q = (T*)C::q(a);
   const int lane = threadIdx.x & 31;
   const int g = lane % M::G;
   const int t = (K == 1) ? 0 : g;
-  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
+  const bool live = SF(a, C::ACTIVE, t, K) != 0.0;
   double vals[1] = {0.0};
   if (K == 1 && !live) {
     // nothing to do for this RHS; still take part in the reduction
   } else {
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / M::G;
     const int ng = (gridDim.x * blockDim.x) / M::G;
-    for (int r = gid; r < a.n_u; r += ng) {
+    for (int r = gid; r < nrows; r += ng) {
       T y = 0;
       if (K == 1) {
-        for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += M::G) y += val[e] * p[a.A_col[e]];
+        for (int e = mptr[r] + g; e < mptr[r + 1]; e += M::G) y += val[e] * p[mcol[e]];
         if (sizeof(T) == 8) y = (T)group_sum<M::G>((double)y);
         else y = (T)group_sumf<M::G>((float)y);
       } else {
-        for (int e = a.A_ptr[r]; e < a.A_ptr[r + 1]; ++e) y += val[e] * p[(size_t)a.A_col[e] * K + t];
+        for (int e = mptr[r]; e < mptr[r + 1]; ++e) y += val[e] * p[(size_t)mcol[e] * K + t];
       }
       if (live && (K > 1 || g == 0)) {
         const size_t idx = (size_t)r * K + t;
@@ -476,7 +550,7 @@ __global__ void k_cg_spmv(Args a) {
     finalize_partials<K, 1>(a.partial, gridDim.x, tot);
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
-      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) SF(a, S_ALPHA, s, K) = SF(a, S_RHO, s, K) / tot[s];
+      if (SF(a, C::ACTIVE, s, K) != 0.0) SF(a, C::ALPHA, s, K) = SF(a, C::RHO, s, K) / tot[s];
     }
     if (threadIdx.x == 0) *a.counter = 0;
   }
@@ -484,20 +558,21 @@ __global__ void k_cg_spmv(Args a) {
 
 // x += alpha p, r -= alpha q, ||r||^2; epilogue: stopping test
 // ||r|| <= inner_tol ||b|| or its == max_inner (or the replayed count).
-template <int K, class T>
+template <int K, class T, int SYS = 0>
 __global__ void k_cg_axpy(Args a) {
-  const T* __restrict__ p = (const T*)a.cg_p;
-  const T* __restrict__ q = (const T*)a.cg_q;
-  T* __restrict__ x = (T*)a.cg_x;
-  T* __restrict__ r = (T*)a.cg_r;
+  using C = CgSys<SYS>;
+  const T* __restrict__ p = (const T*)C::p(a);
+  const T* __restrict__ q = (const T*)C::q(a);
+  T* __restrict__ x = (T*)C::x(a);
+  T* __restrict__ r = (T*)C::r(a);
   const int t = threadIdx.x % K;
-  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
-  const T alpha = live ? (T)SF(a, S_ALPHA, t, K) : (T)0;
+  const bool live = SF(a, C::ACTIVE, t, K) != 0.0;
+  const T alpha = live ? (T)SF(a, C::ALPHA, t, K) : (T)0;
   double vals[1] = {0.0};
   T acc = 0;
   const int stride = (gridDim.x * blockDim.x) / K;
   if (live) {
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < C::n(a); i += stride) {
       const size_t idx = (size_t)i * K + t;
       x[idx] += alpha * p[idx];
       const T rv = r[idx] - alpha * q[idx];
@@ -513,27 +588,27 @@ __global__ void k_cg_axpy(Args a) {
     int any = 0;
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
-      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) {
-        const double its = SF(a, S_CG_ITS, s, K) + 1.0;
-        SF(a, S_CG_ITS, s, K) = its;
-        SF(a, S_INNER_TOTAL, s, K) += 1.0;
+      if (SF(a, C::ACTIVE, s, K) != 0.0) {
+        const double its = SF(a, C::ITS, s, K) + 1.0;
+        SF(a, C::ITS, s, K) = its;
+        SF(a, C::TOTAL, s, K) += 1.0;
         const double rn = sqrt(tot[s]);
-        SF(a, S_RNORM, s, K) = rn;
-        const double target = SF(a, S_CG_TARGET, s, K);
+        SF(a, C::RNORM, s, K) = rn;
+        const double target = SF(a, C::TARGET, s, K);
         bool stop;
         if (target >= 0.0) stop = its >= target;
-        else stop = rn <= a.inner_tol * SF(a, S_CG_BNORM, s, K) || its >= a.max_inner || !isfinite(rn);
+        else stop = rn <= a.inner_tol * SF(a, C::BNORM, s, K) || its >= a.max_inner || !isfinite(rn);
         if (stop) {
-          SF(a, S_CG_ACTIVE, s, K) = 0.0;
-          if (its > SF(a, S_INNER_MAX, s, K)) SF(a, S_INNER_MAX, s, K) = its;
+          SF(a, C::ACTIVE, s, K) = 0.0;
+          if (its > SF(a, C::MAX, s, K)) SF(a, C::MAX, s, K) = its;
         }
       }
-      any = SF(a, S_CG_ACTIVE, s, K) != 0.0;
+      any = SF(a, C::ACTIVE, s, K) != 0.0;
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-      a.flag[1] = any;
-      if (a.use_handles) cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+      a.flag[C::FLAG] = any;
+      if (a.use_handles) cudaGraphSetConditional(C::handle(a), any ? 1u : 0u);
       *a.counter = 0;
     }
   }
@@ -794,18 +869,19 @@ __global__ void k_fill_value(T* __restrict__ x, int64_t n, T v) {
 }
 
 // rho = r^T z.  init: p = z, rho.  Otherwise beta = rho_new / rho.
-template <int K, class T>
+template <int K, class T, int SYS = 0>
 __global__ void k_cg_rho(Args a, int init) {
-  const T* __restrict__ r = (const T*)a.cg_r;
-  const T* __restrict__ z = (const T*)a.cg_z;
-  T* __restrict__ p = (T*)a.cg_p;
+  using C = CgSys<SYS>;
+  const T* __restrict__ r = (const T*)C::r(a);
+  const T* __restrict__ z = (const T*)C::z(a);
+  T* __restrict__ p = (T*)C::p(a);
   const int t = threadIdx.x % K;
-  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;
+  const bool live = SF(a, C::ACTIVE, t, K) != 0.0;
   double vals[1] = {0.0};
   T acc = 0;
   const int stride = (gridDim.x * blockDim.x) / K;
   if (live) {
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < C::n(a); i += stride) {
       const size_t idx = (size_t)i * K + t;
       const T zv = z[idx];
       acc += r[idx] * zv;
@@ -819,12 +895,12 @@ __global__ void k_cg_rho(Args a, int init) {
     finalize_partials<K, 1>(a.partial, gridDim.x, tot);
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
-      if (SF(a, S_CG_ACTIVE, s, K) != 0.0) {
+      if (SF(a, C::ACTIVE, s, K) != 0.0) {
         if (init) {
-          SF(a, S_RHO, s, K) = tot[s];
+          SF(a, C::RHO, s, K) = tot[s];
         } else {
-          SF(a, S_ALPHA, s, K) = tot[s] / SF(a, S_RHO, s, K);  // beta, consumed by k_cg_pupdate
-          SF(a, S_RHO, s, K) = tot[s];
+          SF(a, C::ALPHA, s, K) = tot[s] / SF(a, C::RHO, s, K);  // beta, consumed by k_cg_pupdate
+          SF(a, C::RHO, s, K) = tot[s];
         }
       }
     }
@@ -832,18 +908,85 @@ __global__ void k_cg_rho(Args a, int init) {
   }
 }
 
-// p = z + beta p (beta kept in S_ALPHA between k_cg_rho and this kernel).
-template <int K, class T>
+// p = z + beta p (beta kept in the ALPHA field between k_cg_rho and this kernel).
+template <int K, class T, int SYS = 0>
 __global__ void k_cg_pupdate(Args a) {
-  const T* __restrict__ z = (const T*)a.cg_z;
-  T* __restrict__ p = (T*)a.cg_p;
+  using C = CgSys<SYS>;
+  const T* __restrict__ z = (const T*)C::z(a);
+  T* __restrict__ p = (T*)C::p(a);
   const int t = threadIdx.x % K;
-  if (SF(a, S_CG_ACTIVE, t, K) == 0.0) return;
-  const T beta = (T)SF(a, S_ALPHA, t, K);
+  if (SF(a, C::ACTIVE, t, K) == 0.0) return;
+  const T beta = (T)SF(a, C::ALPHA, t, K);
   const int stride = (gridDim.x * blockDim.x) / K;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < a.n_u; i += stride) {
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < C::n(a); i += stride) {
     const size_t idx = (size_t)i * K + t;
     p[idx] = z[idx] + beta * p[idx];
+  }
+}
+
+// ------------------------------------------------- pressure-block IC(0) ----
+// z = (L L^T)^{-1} r for the IC(0) factor L = L1 x L1 [x L1] of Q (natural
+// numbering), applied one direction at a time: (L L^T)^{-1} is the Kronecker
+// product of Q1^{-1} = L1^{-T} L1^{-1}, so along direction `axis` every line
+// of the pressure grid (m = N + p - 1 points, stride m^(dim-1-axis)) gets a
+// banded forward and backward substitution with L1 (half-bandwidth p - 1):
+//   y_s = (x_s - sum_{o=1}^{p-1} L1[s][s-o] y_{s-o}) / L1[s][s],
+//   z_s = (y_s - sum_{o=1}^{p-1} L1[s+o][s] z_{s+o}) / L1[s][s].
+// One thread per (line, RHS); the lines are independent.  src and dst are
+// distinct buffers (the host alternates them between directions); the
+// values of a line are fetched kQPF steps ahead of their use.
+constexpr int kQPMAX = 6;  // largest velocity degree p (band width of L1)
+constexpr int kQPF = 8;    // prefetch distance along a line
+template <int K, class T>
+__global__ void k_q_lines(Args a, int axis, const T* __restrict__ src, T* __restrict__ dst) {
+  const int m = a.qm, p = a.qp;
+  const T* __restrict__ l1 = pick<T>(a.l1, a.l1_32);
+  int64_t stride = 1;
+  for (int d = a.dim - 1; d > axis; --d) stride *= m;
+  const int64_t nlines = (int64_t)a.n_p / m;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)(tid % K);
+  const int64_t line = tid / K;
+  if (line >= nlines || SF(a, S_Q_ACTIVE, t, K) == 0.0) return;
+  const int64_t base = (line / stride) * stride * m + line % stride;
+  auto at = [&](int s) { return (size_t)(base + (int64_t)s * stride) * K + t; };
+  T win[kQPMAX];  // win[o-1] = the value o steps back along the sweep
+  T pf[kQPF];     // values of the next kQPF points
+#pragma unroll
+  for (int o = 0; o < kQPMAX; ++o) win[o] = T(0);
+#pragma unroll
+  for (int u = 0; u < kQPF; ++u) pf[u] = u < m ? src[at(u)] : T(0);
+  for (int s = 0; s < m; ++s) {
+    T v = pf[0];
+#pragma unroll
+    for (int u = 0; u < kQPF - 1; ++u) pf[u] = pf[u + 1];
+    pf[kQPF - 1] = s + kQPF < m ? src[at(s + kQPF)] : T(0);
+#pragma unroll
+    for (int o = 1; o < kQPMAX; ++o)
+      if (o < p && s - o >= 0) v -= l1[s * p + o] * win[o - 1];
+    v = v / l1[s * p];
+#pragma unroll
+    for (int o = kQPMAX - 1; o > 0; --o) win[o] = win[o - 1];
+    win[0] = v;
+    dst[at(s)] = v;
+  }
+#pragma unroll
+  for (int o = 0; o < kQPMAX; ++o) win[o] = T(0);
+#pragma unroll
+  for (int u = 0; u < kQPF; ++u) pf[u] = m - 1 - u >= 0 ? dst[at(m - 1 - u)] : T(0);
+  for (int s = m - 1; s >= 0; --s) {
+    T v = pf[0];
+#pragma unroll
+    for (int u = 0; u < kQPF - 1; ++u) pf[u] = pf[u + 1];
+    pf[kQPF - 1] = s - kQPF >= 0 ? dst[at(s - kQPF)] : T(0);
+#pragma unroll
+    for (int o = 1; o < kQPMAX; ++o)
+      if (o < p && s + o < m) v -= l1[(s + o) * p + o] * win[o - 1];
+    v = v / l1[s * p];
+#pragma unroll
+    for (int o = kQPMAX - 1; o > 0; --o) win[o] = win[o - 1];
+    win[0] = v;
+    dst[at(s)] = v;
   }
 }
 
@@ -955,18 +1098,21 @@ __global__ void k_adjoint_rhs(int n_u, int n_p, int k, const double* __restrict_
 }
 
 // Operators in natural numbering (one vector, FP64):
-// which 0: y = K x; 1: y = A x_u; 2: y = B x_u; 3: y = B^T x_p.
+// which 0: y = K x; 1: y = A x_u; 2: y = B x_u; 3: y = B^T x_p; 4: y = Q x_p.
 __global__ void k_apply_natural(Args a, int which, const double* __restrict__ xin, double* __restrict__ yout) {
   const int lane = threadIdx.x & 31, g = lane & 7;
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, ng = (gridDim.x * blockDim.x) >> 3;
   const int nu = a.n_u;
-  const int rows = (which == 0) ? nu + a.n_p : (which == 2 ? a.n_p : nu);
+  const int rows = (which == 0) ? nu + a.n_p : ((which == 2 || which == 4) ? a.n_p : nu);
   const double* xu = xin;
   const double* xp = (which == 0) ? xin + nu : xin;
   for (int r = gid; r < rows; r += ng) {
     double y = 0.0;
     int out_index;
-    if ((which == 0 && r < nu) || which == 1 || which == 3) {
+    if (which == 4) {
+      for (int e = a.Q_ptr[r] + g; e < a.Q_ptr[r + 1]; e += 8) y += a.Q_val[e] * xp[a.Q_col[e]];
+      out_index = r;
+    } else if ((which == 0 && r < nu) || which == 1 || which == 3) {
       if (which != 3)
         for (int e = a.A_ptr[r] + g; e < a.A_ptr[r + 1]; e += 8) y += a.A_val[e] * xu[a.order[a.A_col[e]]];
       if (which != 1)

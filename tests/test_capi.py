@@ -57,10 +57,13 @@ def test_struct_layouts_match_header(tmp_path):
 #include "gbstokes.h"
 int main(void) {
   printf("%zu %zu %zu\\n", sizeof(gb_problem), sizeof(gb_solve_opts), sizeof(gb_info));
-  printf("%zu %zu %zu %zu\\n", offsetof(gb_solve_opts, precision), offsetof(gb_solve_opts, use_graph),
-         offsetof(gb_solve_opts, forced_inner_host), offsetof(gb_solve_opts, nforced));
-  printf("%zu %zu %zu %zu\\n", offsetof(gb_info, inner_its_total), offsetof(gb_info, inner_its_max),
-         offsetof(gb_info, relres_true), offsetof(gb_info, status));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gb_solve_opts, precision), offsetof(gb_solve_opts, use_graph),
+         offsetof(gb_solve_opts, forced_inner_host), offsetof(gb_solve_opts, nforced),
+         offsetof(gb_solve_opts, pressure_block), offsetof(gb_solve_opts, forced_q_host),
+         offsetof(gb_solve_opts, nforced_q));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(gb_info, inner_its_total), offsetof(gb_info, inner_its_max),
+         offsetof(gb_info, relres_true), offsetof(gb_info, q_inner_its_total), offsetof(gb_info, q_inner_its_max),
+         offsetof(gb_info, status));
   return 0;
 }
 """)
@@ -71,7 +74,10 @@ int main(void) {
     assert sizes == [C.sizeof(gb.gb_problem), C.sizeof(gb.gb_solve_opts), C.sizeof(gb.gb_info)]
     offs = [int(v) for v in lines[1].split()]
     assert offs == [gb.gb_solve_opts.precision.offset, gb.gb_solve_opts.use_graph.offset,
-                    gb.gb_solve_opts.forced_inner_host.offset, gb.gb_solve_opts.nforced.offset]
+                    gb.gb_solve_opts.forced_inner_host.offset, gb.gb_solve_opts.nforced.offset,
+                    gb.gb_solve_opts.pressure_block.offset, gb.gb_solve_opts.forced_q_host.offset,
+                    gb.gb_solve_opts.nforced_q.offset]
     offs = [int(v) for v in lines[2].split()]
     assert offs == [gb.gb_info.inner_its_total.offset, gb.gb_info.inner_its_max.offset,
-                    gb.gb_info.relres_true.offset, gb.gb_info.status.offset]
+                    gb.gb_info.relres_true.offset, gb.gb_info.q_inner_its_total.offset,
+                    gb.gb_info.q_inner_its_max.offset, gb.gb_info.status.offset]
