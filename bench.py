@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d256")
     ap.add_argument("--ordering", choices=["natural", "rcm", "multicolour"], default="multicolour")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--pressure", choices=["diag", "pcg"], default="diag",
+                    help="pressure block: Diag(Q_nu) or IC(0)-PCG on Q_nu (Sec. 6.4)")
     ap.add_argument("--k", type=int, default=1, help="right-hand sides per solve")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
@@ -194,14 +196,19 @@ def algorithmic_bytes(s, kernel, precision, k):
     raise ValueError(kernel)
 
 
-def launches_per_solve(s, info):
-    """Kernel launches of one solve as the graph driver issues them."""
+def launches_per_solve(s, info, pressure="diag"):
+    """Kernel launches of one solve as the graph driver issues them (the
+    pressure CG adds, per application, dim line-solve passes and a rho
+    kernel, and per iteration an SpMV, an axpy, dim passes, rho, p-update)."""
     L = s.nlevels
-    return (4 + 3 * info["outer_its"] + info["precond_apps"] * (2 * L + 2)
-            + info["inner_its_total"] * (2 * L + 4))
+    n = (4 + 3 * info["outer_its"] + info["precond_apps"] * (2 * L + 2)
+         + info["inner_its_total"] * (2 * L + 4))
+    if pressure == "pcg":
+        n += info["precond_apps"] * (s.dim + 1) + info["q_inner_its_total"] * (s.dim + 4)
+    return n
 
 
-def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0):
+def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0, pressure="diag"):
     """The oracle as it stands, single-threaded, on a bounded sample of one
     solve: the first m MINRES iterations, extrapolated to the full solve."""
     import numpy as np
@@ -210,14 +217,15 @@ def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0):
     from paper_1309_5048_gb300.inputs import fourier_modes
     P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=ordering)
     P.factor()
+    P.factor_q()
     kappa, amp = fourier_modes(W["dim"], seed=0)
     b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
     t = time.perf_counter()
-    P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2)
+    P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2, pressure=pressure)
     pilot = (time.perf_counter() - t) / 2
     m = int(max(2, min(outer_full, target_s / max(pilot, 1e-6))))
     t = time.perf_counter()
-    _, info = P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=m)
+    _, info = P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=m, pressure=pressure)
     dt = time.perf_counter() - t
     per_outer = dt / max(info["outer"], 1)
     est = per_outer * max(outer_full, 1)
@@ -239,20 +247,22 @@ def run_reference(args):
     W = WORKLOADS[args.workload]
     P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=args.ordering)
     P.factor()
+    P.factor_q()
     kappa, amp = fourier_modes(W["dim"], seed=0)
     b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
+    pres = dict(pressure=args.pressure)
     # one untimed full solve gives the outer count used to extrapolate samples
     t = time.perf_counter()
-    x, full = P.minres(b, tol=args.tol, inner_tol=args.inner_tol)
+    x, full = P.minres(b, tol=args.tol, inner_tol=args.inner_tol, **pres)
     t_full = time.perf_counter() - t
     outer_full = max(full["outer"], 1)
     per_outer_full = t_full / outer_full
     m = int(max(1, min(outer_full, 4.0 / max(per_outer_full, 1e-6))))  # ~4 s per step
     for _ in range(args.warmup):
-        P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m)
+        P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m, **pres)
     t = time.perf_counter()
     for _ in range(args.steps):
-        _, info = P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m)
+        _, info = P.minres(b, tol=args.tol, inner_tol=args.inner_tol, max_outer=m, **pres)
     dt = time.perf_counter() - t
     per_solve = dt / args.steps / max(info["outer"], 1) * outer_full
     value = 1.0 / per_solve
@@ -263,7 +273,8 @@ def run_reference(args):
             "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["desc"], "ordering": args.ordering, "k": 1, "tol": args.tol,
-                       "inner_tol": args.inner_tol},
+                       "inner_tol": args.inner_tol,
+                       "pressure_block": "Diag(Q)" if args.pressure == "diag" else "IC(0)-PCG(Q)"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "outer_its": outer_full, "relres_true": full["relres_true"]}
@@ -310,7 +321,7 @@ def main():
     rhs = make_rhs(k, rank * 1000)
     out = torch.empty_like(rhs)
     opts = dict(tol=args.tol, inner_tol=args.inner_tol, precision=args.precision, use_graph=not args.no_graph,
-                max_outer=args.max_outer)
+                max_outer=args.max_outer, pressure=args.pressure)
 
     def timed(rhs_, out_, steps, warmup, **o):
         info = None
@@ -384,21 +395,27 @@ def main():
 
     variants = {}
     if not args.no_variants and rank == 0:
-        for name, prec, kk in (("mixed_k1", "mixed", 1), ("fp64_k32", "fp64", 32), ("mixed_k32", "mixed", 32)):
+        # Diag(Q_nu) pressure block (the configuration above) in other
+        # precisions / batch widths, and the paper's IC(0)-PCG(A,Q) block
+        for name, prec, kk, pres in (("mixed_k1", "mixed", 1, "diag"), ("fp64_k32", "fp64", 32, "diag"),
+                                     ("mixed_k32", "mixed", 32, "diag"), ("fp64_k1_pcgq", "fp64", 1, "pcg"),
+                                     ("mixed_k1_pcgq", "mixed", 1, "pcg"), ("mixed_k32_pcgq", "mixed", 32, "pcg")):
             r = make_rhs(kk, 5000)
             o = torch.empty_like(r)
             st = 1 if kk > 1 else max(1, args.steps // 2)
             ms_v, inf_v = timed(r, o, st, 1, tol=args.tol, inner_tol=args.inner_tol, precision=prec,
-                                use_graph=not args.no_graph)
+                                use_graph=not args.no_graph, pressure=pres)
             iv = inf_v if isinstance(inf_v, list) else [inf_v]
             variants[name] = {"solves_per_s": st * kk / (ms_v / 1000.0), "k": kk, "precision": prec,
+                              "pressure_block": "Diag(Q)" if pres == "diag" else "IC(0)-PCG(Q)",
                               "outer_its_mean": statistics.mean(i["outer_its"] for i in iv),
                               "inner_its_mean": statistics.mean(i["inner_its_total"] for i in iv),
                               "relres_true_max": max(i["relres_true"] for i in iv)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(W, args.ordering, args.tol, args.inner_tol, int(infos[0]["outer_its"]))
+        cpu = cpu_baseline(W, args.ordering, args.tol, args.inner_tol, int(infos[0]["outer_its"]),
+                           pressure=args.pressure)
 
     if rank == 0:
         line = {
@@ -407,6 +424,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
             "config": {"workload": W["desc"], "ordering": args.ordering, "k": k, "precision": args.precision,
+                       "pressure_block": "Diag(Q)" if args.pressure == "diag" else "IC(0)-PCG(Q)",
                        "tol": args.tol, "inner_tol": args.inner_tol, "graph": not args.no_graph,
                        "l2": "no flush: per-iteration working set (A, L, L^T, vectors) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -415,7 +433,7 @@ def main():
             "e2e": {"value": throughput(world, args.steps, k, 1000.0 * e2e_s), "unit": "solves/s",
                     "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
-            "gpu_launches": int(args.steps * sum(launches_per_solve(s, i) for i in infos)),
+            "gpu_launches": int(args.steps * sum(launches_per_solve(s, i, args.pressure) for i in infos)),
             "clocks": clock_info,
             "outer_its": infos[0]["outer_its"], "inner_its_total": infos[0]["inner_its_total"],
             "inner_its_mean": infos[0]["inner_its_total"] / max(infos[0]["precond_apps"], 1),
