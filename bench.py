@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d256")
     ap.add_argument("--ordering", choices=["natural", "rcm", "multicolour"], default="multicolour")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--spmv", choices=["auto", "csr", "sell"], default="auto",
+                    help="single-RHS SpMV layout of the benchmark precision (auto: timed at the first solve)")
+    ap.add_argument("--trsv", choices=["auto", "csr", "sell", "staged4", "staged12", "staged32"], default="auto",
+                    help="single-RHS IC(0) sweep layout of the benchmark precision")
     ap.add_argument("--pressure", choices=["diag", "pcg"], default="diag",
                     help="pressure block: Diag(Q_nu) or IC(0)-PCG on Q_nu (Sec. 6.4)")
     ap.add_argument("--k", type=int, default=1, help="right-hand sides per solve")
@@ -307,6 +311,8 @@ def main():
     t0 = time.perf_counter()
     s.assemble(1.0)
     s.factor_ic0()
+    if args.spmv != "auto" or args.trsv != "auto":
+        s.set_kernel_variants(args.precision, args.spmv, args.trsv)
     torch.cuda.synchronize()
     t_rf = time.perf_counter() - t0
     k = args.k
