@@ -169,9 +169,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel, workload):
+def traffic_for(kernel, workload, trsv=None, precision=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current kernel sources with the same sweep layout and precision;
+    else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -180,6 +181,8 @@ def traffic_for(kernel, workload):
         return None
     e = d.get(workload, {}).get(kernel)
     if not e or e.get("src_hash") != source_hash():
+        return None
+    if e.get("trsv", trsv) != trsv or e.get("precision", precision) != precision:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -394,7 +397,7 @@ def main():
     peak, peak_kind = measured_peak()
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": kern[dom]["gbs"] / peak, "peak_source": peak_kind,
-            "traffic": traffic_for(dom, args.workload),
+            "traffic": traffic_for(dom, args.workload, s.kernel_variants(args.precision)[1], args.precision),
             "unit_of_launch": ("one preconditioner application: forward + backward IC(0) sweep over %d levels "
                                "each" % s.nlevels) if dom == "ic0_apply" else "one kernel launch"}
     del x_last
