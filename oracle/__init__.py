@@ -76,13 +76,13 @@ def lib():
             L.or_load_manufactured.argtypes = [vp, vp]
             L.or_manufactured_errors.argtypes = [vp, vp, vp, vp]
             L.or_manufactured_point.argtypes = [dbl, dbl, dbl, vp]
-            L.or_minres.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, vp, i64, i32, vp, i64, vp]
+            L.or_minres.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, vp, i64, i32, vp, i64, i32, i32, vp]
             L.or_counts.restype = i64
             L.or_counts.argtypes = [vp, vp, i64]
             L.or_qcounts.restype = i64
             L.or_qcounts.argtypes = [vp, vp, i64]
             L.or_hist.restype = i64
-            L.or_hist.argtypes = [vp, vp, i64]
+            L.or_hist.argtypes = [vp, i32, vp, i64]
             L.or_pcg.argtypes = [vp, vp, vp, dbl, i32]
             L.or_pcg_q.argtypes = [vp, vp, vp, dbl, i32]
             L.or_precond.argtypes = [vp, vp, vp, dbl, i32, i32]
@@ -100,7 +100,9 @@ def _p(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-PRESSURE_BLOCKS = {"diag": 0, "pcg": 1}
+PRESSURE_BLOCKS = {"diag": 0, "pcg": 1, "jacobi_pcg": 2}
+VELOCITY_BLOCKS = {"ic0_pcg": 0, "diag": 1, "jacobi_pcg": 2}
+STOP_RULES = {"residual": 0, "estimate": 1}
 
 
 def default_cpen(p: int) -> float:
@@ -237,13 +239,17 @@ class Problem:
         return y
 
     def minres(self, b, tol=1e-8, inner_tol=1e-2, max_outer=5000, max_inner=1000, forced=None,
-               pressure="diag", forced_q=None):
+               pressure="diag", forced_q=None, velocity="ic0_pcg", stop="residual"):
         """Preconditioned MINRES from x0 = 0; pressure filtered to zero mean.
-        pressure: 'diag' (Diag(Q_nu)) or 'pcg' (IC(0)-PCG on Q_nu, needs
-        factor_q()).  Returns (x, info dict with outer, relres_est,
-        relres_true, status, counts (inner its per preconditioner
+        stop: 'residual' (||b - K x|| / ||b|| <= tol, recomputed every step)
+        or 'estimate' (|eta| / gamma_1 <= tol).
+        velocity: 'ic0_pcg' (IC(0)-PCG on A_h, needs factor()), 'diag'
+        (Diag(A_h)) or 'jacobi_pcg' (diagonally preconditioned CG).
+        pressure: 'diag' (Diag(Q_nu)), 'pcg' (IC(0)-PCG on Q_nu, needs
+        factor_q()) or 'jacobi_pcg'.  Returns (x, info dict with outer,
+        relres_est, relres_true, status, counts (inner its per preconditioner
         application), qcounts (pressure CG its per application), hist)."""
-        if not self.factored or (pressure == "pcg" and not self.qfactored):
+        if (velocity == "ic0_pcg" and not self.factored) or (pressure == "pcg" and not self.qfactored):
             raise RuntimeError("factor() (and factor_q() for pressure='pcg') first")
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
@@ -252,7 +258,8 @@ class Problem:
         fq = None if forced_q is None else np.ascontiguousarray(forced_q, dtype=np.int32)
         rc = lib().or_minres(self._h, _p(b), _p(x), tol, inner_tol, max_outer, max_inner,
                              _p(fc), 0 if fc is None else len(fc), PRESSURE_BLOCKS[pressure],
-                             _p(fq), 0 if fq is None else len(fq), _p(info))
+                             _p(fq), 0 if fq is None else len(fq), VELOCITY_BLOCKS[velocity],
+                             STOP_RULES[stop], _p(info))
         if rc != 0:
             raise RuntimeError(lib().or_last_error().decode())
         n = lib().or_counts(self._h, None, 0)
@@ -261,12 +268,15 @@ class Problem:
         nq = lib().or_qcounts(self._h, None, 0)
         qcounts = np.zeros(max(nq, 1), np.int32)
         lib().or_qcounts(self._h, _p(qcounts), nq)
-        nh = lib().or_hist(self._h, None, 0)
+        nh = lib().or_hist(self._h, 0, None, 0)
         hist = np.zeros(max(nh, 1))
-        lib().or_hist(self._h, _p(hist), nh)
+        lib().or_hist(self._h, 0, _p(hist), nh)
+        nh2 = lib().or_hist(self._h, 1, None, 0)
+        hist2 = np.zeros(max(nh2, 1))
+        lib().or_hist(self._h, 1, _p(hist2), nh2)
         return x, dict(outer=int(info[0]), relres_est=float(info[1]), relres_true=float(info[2]),
                        status=int(info[3]), counts=counts[:n].copy(), qcounts=qcounts[:nq].copy(),
-                       hist=hist[:nh].copy())
+                       hist=hist[:nh].copy(), hist_res=hist2[:nh2].copy())
 
     def pcg(self, b, inner_tol, max_inner=1000):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -19,7 +19,7 @@ struct Handle {
   std::vector<int32_t> level, rlevel;
   bool factored = false;
   std::vector<int32_t> counts;
-  std::vector<double> hist;
+  std::vector<double> hist, hist2;
   // pressure mass matrix: ordering, IC(0) factor and its levels
   std::vector<int32_t> permQ;
   Csr LQ;
@@ -197,19 +197,19 @@ void or_manufactured_point(double nu, double x, double y, double* out) {
 // forced_q replay the inner counts of the velocity / pressure CG.
 int or_minres(void* hv, const double* b, double* x, double tol, double inner_tol, int max_outer,
               int max_inner, const int32_t* forced, int64_t nforced, int pressure,
-              const int32_t* forced_q, int64_t nforced_q, double* info) {
+              const int32_t* forced_q, int64_t nforced_q, int velocity, int stop_rule, double* info) {
   Handle* h = static_cast<Handle*>(hv);
-  if (!h->factored || (pressure == PRESSURE_PCG && !h->qfactored)) {
+  if ((velocity == VELOCITY_IC0_PCG && !h->factored) || (pressure == PRESSURE_PCG && !h->qfactored)) {
     g_err = "factor first";
     return -1;
   }
   OR_TRY(Precond M; M.P = &h->P; M.L = &h->L; M.perm = &h->perm; M.inner_tol = inner_tol;
          M.max_inner = max_inner; M.forced = forced; M.nforced = forced ? nforced : 0;
-         M.pressure = pressure; M.LQ = &h->LQ; M.permQ = &h->permQ; M.forced_q = forced_q;
-         M.nforced_q = forced_q ? nforced_q : 0;
-         MinresInfo mi; minres(h->P, M, b, x, tol, max_outer, mi);
+         M.pressure = pressure; M.velocity = velocity; M.LQ = &h->LQ; M.permQ = &h->permQ;
+         M.forced_q = forced_q; M.nforced_q = forced_q ? nforced_q : 0;
+         MinresInfo mi; minres(h->P, M, b, x, tol, max_outer, mi, stop_rule);
          pressure_filter(h->P, x + h->P.n_u); h->counts = M.counts; h->qcounts = M.qcounts;
-         h->hist = mi.hist; info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
+         h->hist = mi.hist; h->hist2 = mi.hist2; info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
          info[3] = mi.status; return 0;)
 }
 
@@ -227,10 +227,12 @@ int64_t or_counts(void* hv, int32_t* out, int64_t cap) {
   return n;
 }
 
-int64_t or_hist(void* hv, double* out, int64_t cap) {
+// which 0: |eta|/gamma_1 after each step; 1: ||b - K x_j|| / ||b|| (STOP_RESIDUAL)
+int64_t or_hist(void* hv, int which, double* out, int64_t cap) {
   Handle* h = static_cast<Handle*>(hv);
-  int64_t n = (int64_t)h->hist.size();
-  for (int64_t i = 0; i < n && i < cap; ++i) out[i] = h->hist[i];
+  const std::vector<double>& v = which ? h->hist2 : h->hist;
+  int64_t n = (int64_t)v.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
   return n;
 }
 

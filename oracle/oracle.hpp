@@ -110,9 +110,14 @@ void level_sets(const Csr& L, std::vector<int32_t>& level, std::vector<int32_t>&
 int64_t ic0(const Csr& A, const std::vector<int32_t>& perm, Csr& L);
 
 // Pressure block of the preconditioner (Sec. 5.1): Diag(Q_nu), or Q_nu
-// approximated by an IC(0)-preconditioned CG solve ("IC(0)-PCG(A,Q)",
-// Sec. 6.4) with the same relative tolerance and cap as the velocity block.
-enum PressureBlock { PRESSURE_DIAG = 0, PRESSURE_PCG = 1 };
+// approximated by a CG solve with the same relative tolerance and cap as the
+// velocity block, preconditioned by IC(0) of Q ("IC(0)-PCG(A,Q)", Sec. 6.4)
+// or by the diagonal of Q ("PCG(A,Q)", Sec. 6.2).
+enum PressureBlock { PRESSURE_DIAG = 0, PRESSURE_PCG = 1, PRESSURE_JACOBI_PCG = 2 };
+// Velocity block (Sec. 5.1): a CG solve with A_h preconditioned by IC(0)
+// ("PCG(A)" of Sec. 6.4), Diag(A_h) ("Diag(A,Q)"), or a CG solve
+// preconditioned by the diagonal of A_h ("PCG(A)" of Sec. 6.2).
+enum VelocityBlock { VELOCITY_IC0_PCG = 0, VELOCITY_DIAG = 1, VELOCITY_JACOBI_PCG = 2 };
 
 struct Precond {
   const Problem* P;
@@ -123,6 +128,7 @@ struct Precond {
   const int32_t* forced = nullptr;  // replay: inner counts per application
   int64_t nforced = 0;
   int pressure = PRESSURE_DIAG;
+  int velocity = VELOCITY_IC0_PCG;
   const Csr* LQ = nullptr;       // IC(0) factor of Q (PRESSURE_PCG)
   const std::vector<int32_t>* permQ = nullptr;
   const int32_t* forced_q = nullptr;  // replay: pressure CG counts per application
@@ -131,20 +137,28 @@ struct Precond {
   std::vector<int32_t> counts;   // inner iterations of each application
   std::vector<int32_t> qcounts;  // pressure CG iterations of each application
 };
+// MINRES stopping rule: the 2-norm relative residual ||b - K x_j|| / ||b||
+// (the paper's "relative residual", Sec. 6.2; it reproduces the iteration
+// counts of Table niter_square_k_2), or the recurrence's M^{-1}-norm
+// estimate |eta_j| / gamma_1 (eq. minimax_precond).
+enum StopRule { STOP_RESIDUAL = 0, STOP_ESTIMATE = 1 };
 struct MinresInfo {
   int outer = 0;
   double relres_est = 0, relres_true = 0;
   int status = 0;  // 0 converged, 1 hit max_outer, 2 breakdown
-  std::vector<double> hist;  // |eta|/gamma_1 after each step
+  std::vector<double> hist;   // |eta|/gamma_1 after each step
+  std::vector<double> hist2;  // ||b - K x_j|| / ||b|| after each step (STOP_RESIDUAL)
 };
 void spmv(const Csr& M, const double* x, double* y);
 void stokes_apply(const Problem& P, const double* x, double* y);
 int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced_its);
 // The same CG on the pressure mass matrix Q with its IC(0) factor.
 int pcg_ic0_q(const Problem& P, Precond& M, const double* b, double* x, int forced_its);
+// CG with the diagonal (Jacobi) preconditioner of Mat, same stopping rule.
+int pcg_jacobi(const Csr& Mat, double tol, int max_it, const double* b, double* x, int forced_its);
 void precond_apply(const Problem& P, Precond& M, const double* r, double* z);
 void minres(const Problem& P, Precond& M, const double* b, double* x, double tol,
-            int max_outer, MinresInfo& info);
+            int max_outer, MinresInfo& info, int stop_rule = STOP_RESIDUAL);
 void pressure_filter(const Problem& P, double* pres);
 
 }  // namespace oracle

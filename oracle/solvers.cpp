@@ -136,6 +136,43 @@ static int pcg(const Csr& Mat, const Csr& L, const std::vector<int32_t>& perm, d
   return it;
 }
 
+// CG with the Jacobi preconditioner z = r / diag(Mat) (Sec. 6.2: "the
+// preconditioner is simply the diagonal"), same iteration as pcg() above.
+int pcg_jacobi(const Csr& Mat, double tol, int max_it, const double* b, double* x, int forced_its) {
+  const int64_t n = Mat.nrows;
+  std::vector<double> d(n);
+  for (int64_t i = 0; i < n; ++i) d[i] = Mat.val[Mat.find(i, (int32_t)i)];
+  for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  const double bnorm = std::sqrt(dot(b, b, n));
+  if (bnorm == 0.0 || forced_its == 0) return 0;
+  std::vector<double> r(b, b + n), z(n), p(n), q(n);
+  for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+  p = z;
+  double rho = dot(r.data(), z.data(), n);
+  int it = 0;
+  for (;;) {
+    spmv(Mat, p.data(), q.data());
+    ++it;
+    const double alpha = rho / dot(p.data(), q.data(), n);
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    if (forced_its > 0) {
+      if (it >= forced_its) break;
+    } else {
+      const double rnorm = std::sqrt(dot(r.data(), r.data(), n));
+      if (rnorm <= tol * bnorm || it >= max_it) break;
+    }
+    for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+    const double rho_new = dot(r.data(), z.data(), n);
+    const double beta = rho_new / rho;
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rho = rho_new;
+  }
+  return it;
+}
+
 // Inner CG on A_h (Sec. 5.1 "PCG(A)").
 int pcg_ic0(const Problem& P, Precond& M, const double* b, double* x, int forced_its) {
   return pcg(P.A, *M.L, *M.perm, M.inner_tol, M.max_inner, b, x, forced_its);
@@ -157,16 +194,25 @@ void precond_apply(const Problem& P, Precond& M, const double* r, double* z) {
     if (app >= M.nforced) throw std::runtime_error("replay: ran out of forced counts");
     forced = M.forced[app];
   }
-  int its = pcg_ic0(P, M, r, z, forced);
+  int its = 0;
+  if (M.velocity == VELOCITY_DIAG) {
+    for (int64_t i = 0; i < P.n_u; ++i) z[i] = r[i] / P.A.val[P.A.find(i, (int32_t)i)];
+  } else if (M.velocity == VELOCITY_JACOBI_PCG) {
+    its = pcg_jacobi(P.A, M.inner_tol, M.max_inner, r, z, forced);
+  } else {
+    its = pcg_ic0(P, M, r, z, forced);
+  }
   M.counts.push_back(its);
-  if (M.pressure == PRESSURE_PCG) {
+  if (M.pressure == PRESSURE_PCG || M.pressure == PRESSURE_JACOBI_PCG) {
     int forced_q = -1;
     if (M.forced_q) {
       if (app >= M.nforced_q) throw std::runtime_error("replay: ran out of forced pressure counts");
       forced_q = M.forced_q[app];
     }
     std::vector<double> y(P.n_p);
-    M.qcounts.push_back(pcg_ic0_q(P, M, r + P.n_u, y.data(), forced_q));
+    M.qcounts.push_back(M.pressure == PRESSURE_PCG
+                            ? pcg_ic0_q(P, M, r + P.n_u, y.data(), forced_q)
+                            : pcg_jacobi(P.Q, M.inner_tol, M.max_inner, r + P.n_u, y.data(), forced_q));
     for (int64_t k = 0; k < P.n_p; ++k) z[P.n_u + k] = 2.0 * P.nu * y[k];
     return;
   }
@@ -179,10 +225,12 @@ void precond_apply(const Problem& P, Precond& M, const double* r, double* z) {
 // Preconditioned MINRES (Sec. 5, eq. opt_condition with the M^{-1}-norm of
 // eq. linsys_precond): Lanczos three-term recurrence in the M^{-1} inner
 // product, QR of the tridiagonal matrix by Givens rotations, update of x by
-// the search directions w.  eta tracks ||r_j||_{M^{-1}}; the solve stops when
-// |eta| / gamma_1 <= tol.  Zero initial guess.
+// the search directions w.  eta tracks ||r_j||_{M^{-1}}.  The solve stops when
+// ||b - K x_j||_2 / ||b||_2 <= tol (STOP_RESIDUAL, the residual recomputed
+// from x_j after every step) or when |eta| / gamma_1 <= tol (STOP_ESTIMATE).
+// Zero initial guess.
 void minres(const Problem& P, Precond& M, const double* b, double* x, double tol,
-            int max_outer, MinresInfo& info) {
+            int max_outer, MinresInfo& info, int stop_rule) {
   const int64_t n = P.n_u + P.n_p;
   std::vector<double> v_prev(n, 0.0), v(b, b + n), v_next(n), z(n), z_next(n), q(n);
   std::vector<double> w_prev(n, 0.0), w(n, 0.0), w_next(n);
@@ -240,7 +288,15 @@ void minres(const Problem& P, Precond& M, const double* b, double* x, double tol
     info.outer = j;
     info.relres_est = std::fabs(eta) / gamma1;
     info.hist.push_back(info.relres_est);
-    if (info.relres_est <= tol) {
+    double rel = info.relres_est;
+    if (stop_rule == STOP_RESIDUAL) {
+      stokes_apply(P, x, q.data());
+      double rr = 0.0;
+      for (int64_t i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+      rel = std::sqrt(rr) / bnorm;
+      info.hist2.push_back(rel);
+    }
+    if (rel <= tol) {
       info.status = 0;
       break;
     }
