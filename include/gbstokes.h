@@ -76,6 +76,28 @@ extern "C" {
  * pressure CG normally stops after one iteration. */
 #define GB_PRESSURE_DIAG 0
 #define GB_PRESSURE_PCG 1
+/* GB_PRESSURE_JACOBI_PCG: the CG solve with Q_nu preconditioned by its
+ * diagonal ("PCG(A,Q)" of Sec. 6.2). */
+#define GB_PRESSURE_JACOBI_PCG 2
+
+/* Velocity block M_A of the preconditioner (Sec. 5.1).
+ * GB_VELOCITY_IC0_PCG: CG on A_h preconditioned by IC(0) ("PCG(A)", Sec. 6.4);
+ * GB_VELOCITY_DIAG: M_A = Diag(A_h) ("Diag(A,Q)");
+ * GB_VELOCITY_JACOBI_PCG: CG on A_h preconditioned by its diagonal
+ * ("PCG(A)", Sec. 6.2).  The CG blocks stop at ||r|| <= inner_tol ||b||. */
+#define GB_VELOCITY_IC0_PCG 0
+#define GB_VELOCITY_DIAG 1
+#define GB_VELOCITY_JACOBI_PCG 2
+
+/* MINRES stopping rule.
+ * GB_STOP_RESIDUAL: ||b - K x_j||_2 / ||b||_2 <= tol after step j, the
+ * paper's relative residual (it reproduces the MINRES counts of the paper's
+ * square-domain tables); the residual is carried by the recurrence
+ * r_j = r_{j-1} - c_{j+1} eta_j K w_{j+1} with K w from the Lanczos products.
+ * GB_STOP_ESTIMATE: |eta_j| / gamma_1 <= tol, the M^{-1}-norm residual
+ * ratio of the Lanczos/Givens recurrence (eq. minimax_precond). */
+#define GB_STOP_RESIDUAL 0
+#define GB_STOP_ESTIMATE 1
 
 typedef struct gb_ctx gb_ctx;
 
@@ -87,8 +109,7 @@ typedef struct {
 } gb_problem;
 
 typedef struct {
-  double tol;       /* outer stop: |eta_j| / gamma_1 <= tol (M^{-1}-norm residual
-                       ratio of eq. minimax_precond) */
+  double tol;       /* outer stop tolerance (see stop_rule) */
   double inner_tol; /* inner CG stop: ||r||_2 <= inner_tol ||b||_2 from x_0 = 0 */
   int precision;    /* GB_PREC_* */
   int max_outer;    /* MINRES iteration cap (>= 1) */
@@ -105,6 +126,8 @@ typedef struct {
                        (GB_PRESSURE_PCG, k == 1): the i-th application runs
                        exactly forced_q_host[i] iterations.  NULL otherwise. */
   int64_t nforced_q; /* length of forced_q_host */
+  int stop_rule;      /* GB_STOP_* (0: the 2-norm relative residual) */
+  int velocity_block; /* GB_VELOCITY_* (0: IC(0)-preconditioned CG) */
 } gb_solve_opts;
 
 typedef struct {
@@ -112,7 +135,7 @@ typedef struct {
   int precond_apps;    /* preconditioner applications (outer_its + 1) */
   int64_t inner_its_total; /* inner CG iterations over all applications */
   int inner_its_max;   /* largest inner count of one application */
-  double relres_est;   /* |eta| / gamma_1 at exit */
+  double relres_est;   /* |eta| / gamma_1 at exit (recurrence estimate) */
   double relres_true;  /* ||b - K x||_2 / ||b||_2 recomputed at exit */
   int64_t q_inner_its_total; /* pressure CG iterations (GB_PRESSURE_PCG) */
   int q_inner_its_max;       /* largest pressure CG count of one application */

@@ -21,7 +21,9 @@ _lib = None
 
 ORDERINGS = {"natural": 0, "rcm": 1, "multicolour": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-PRESSURE_BLOCKS = {"diag": 0, "pcg": 1}
+PRESSURE_BLOCKS = {"diag": 0, "pcg": 1, "jacobi_pcg": 2}
+VELOCITY_BLOCKS = {"ic0_pcg": 0, "diag": 1, "jacobi_pcg": 2}
+STOP_RULES = {"residual": 0, "estimate": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "IC(0) breakdown",
           5: "not converged", 6: "non-finite value", 7: "device wait timed out"}
 GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_IC0_BREAKDOWN = 0, 5, 4
@@ -41,7 +43,8 @@ class gb_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("precision", C.c_int),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("use_graph", C.c_int),
                 ("forced_inner_host", C.c_void_p), ("nforced", C.c_int64), ("pressure_block", C.c_int),
-                ("forced_q_host", C.c_void_p), ("nforced_q", C.c_int64)]
+                ("forced_q_host", C.c_void_p), ("nforced_q", C.c_int64), ("stop_rule", C.c_int),
+                ("velocity_block", C.c_int)]
 
 
 class gb_info(C.Structure):
@@ -191,9 +194,10 @@ class Stokes:
     # ------------------------------------------------------------ solves
     @staticmethod
     def options(tol=1e-8, inner_tol=1e-2, precision="fp64", max_outer=5000, max_inner=1000,
-                use_graph=True, forced=None, pressure="diag", forced_q=None):
+                use_graph=True, forced=None, pressure="diag", forced_q=None, stop="residual",
+                velocity="ic0_pcg"):
         o = gb_solve_opts(tol, inner_tol, PRECISIONS[precision], max_outer, max_inner, int(use_graph), None, 0,
-                          PRESSURE_BLOCKS[pressure], None, 0)
+                          PRESSURE_BLOCKS[pressure], None, 0, STOP_RULES[stop], VELOCITY_BLOCKS[velocity])
         keep = []
         if forced is not None:
             f = np.ascontiguousarray(forced, dtype=np.int32)
@@ -224,9 +228,11 @@ class Stokes:
     def solve(self, rhs, out=None, **kw):
         """Preconditioned MINRES from x0 = 0 for rhs of shape (n,) or (k, n),
         k <= 32.  Options: tol, inner_tol, precision ('fp64'|'mixed'),
-        max_outer, max_inner, use_graph, pressure ('diag': Diag(Q_nu),
-        'pcg': IC(0)-PCG on Q_nu), forced / forced_q (replay the velocity /
-        pressure inner counts)."""
+        max_outer, max_inner, use_graph, stop ('residual': ||b - Kx|| / ||b||
+        <= tol, the default; 'estimate': |eta| / gamma_1 <= tol), velocity
+        ('ic0_pcg', 'diag', 'jacobi_pcg'), pressure ('diag': Diag(Q_nu),
+        'pcg': IC(0)-PCG on Q_nu, 'jacobi_pcg'), forced / forced_q (replay
+        the velocity / pressure inner counts)."""
         return self._solve(load_library().gb_solve, rhs, out, **kw)
 
     def solve_adjoint(self, grad, out=None, **kw):

@@ -113,6 +113,8 @@ struct Workspace {
   double* W[3] = {nullptr, nullptr, nullptr};
   double* q = nullptr;
   double* b = nullptr;  // right-hand side, internal layout
+  double* R = nullptr;  // residual b - K x_j (2-norm stopping rule)
+  double* KW[3] = {nullptr, nullptr, nullptr};  // K w_j, rotating like W
   // inner CG, element type T (double or float) stored as raw bytes
   void* cg_x = nullptr;
   void* cg_r = nullptr;

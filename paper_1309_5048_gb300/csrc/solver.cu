@@ -49,6 +49,8 @@ void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
     for (int i = 0; i < 3; ++i) w.W[i] = (double*)dmalloc(vb);
     w.q = (double*)dmalloc(vb);
     w.b = (double*)dmalloc(vb);
+    w.R = (double*)dmalloc(vb);
+    for (int i = 0; i < 3; ++i) w.KW[i] = (double*)dmalloc(vb);
     w.cg_x = dmalloc(cb);
     w.cg_r = dmalloc(cb);
     w.cg_z = dmalloc(cb);
@@ -167,8 +169,17 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.qcg_p = w.qcg_p;
   a.qcg_q = w.qcg_q;
   a.pressure_block = GB_PRESSURE_DIAG;
+  a.velocity_block = GB_VELOCITY_IC0_PCG;
+  a.stop_rule = GB_STOP_RESIDUAL;
+  a.A_diag = c.A_diag.p;
+  a.R = w.R;
+  a.KW0 = w.KW[0];
+  a.KW1 = w.KW[1];
+  a.KW2 = w.KW[2];
   if (o) {
     a.pressure_block = o->pressure_block;
+    a.velocity_block = o->velocity_block;
+    a.stop_rule = o->stop_rule;
     a.forced_q = o->forced_q_host ? w.forced_q : nullptr;
     a.nforced_q = o->forced_q_host ? (int)o->nforced_q : 0;
     a.tol = o->tol;
@@ -307,9 +318,18 @@ struct Run {
   void trsv_bwd() {
     for (int l = c.nlev - 1; l >= 0; --l) level<false>(l);
   }
+  // M^{-1} r of the velocity CG: the IC(0) sweeps, or the diagonal
+  bool vel_cg() const { return a.velocity_block != GB_VELOCITY_DIAG; }
+  void vel_precond() {
+    if (a.velocity_block == GB_VELOCITY_JACOBI_PCG) {
+      k_jacobi<K, T, 0><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
+    } else {
+      trsv_fwd();
+      trsv_bwd();
+    }
+  }
   void cg_prologue() {
-    trsv_fwd();
-    trsv_bwd();
+    vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 1);
   }
   void cg_head() {
@@ -317,15 +337,18 @@ struct Run {
     k_cg_axpy<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
   void cg_tail() {
-    trsv_fwd();
-    trsv_bwd();
+    vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 0);
     k_cg_pupdate<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
   // Pressure-block CG on Q (GB_PRESSURE_PCG): the IC(0) application is one
   // pass of banded line solves per direction, alternating between the
   // z and q buffers so that the last pass lands in z.
-  bool pcg_q() const { return a.pressure_block == GB_PRESSURE_PCG; }
+  bool pcg_q() const { return a.pressure_block != GB_PRESSURE_DIAG; }
+  void q_precond() {
+    if (a.pressure_block == GB_PRESSURE_JACOBI_PCG) k_jacobi<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a);
+    else q_lines();
+  }
   void q_lines() {
     const int64_t threads = (int64_t)c.n_p / (c.N + c.p - 1) * K;
     const int grid = (int)((threads + 127) / 128);
@@ -337,7 +360,7 @@ struct Run {
     }
   }
   void qcg_prologue() {
-    q_lines();
+    q_precond();
     k_cg_rho<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a, 1);
   }
   void qcg_head() {
@@ -345,7 +368,7 @@ struct Run {
     k_cg_axpy<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a);
   }
   void qcg_tail() {
-    q_lines();
+    q_precond();
     k_cg_rho<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a, 0);
     k_cg_pupdate<K, T, 1><<<grid_cap(c.n_p * K), kBlock, 0, s>>>(a);
   }
@@ -360,7 +383,7 @@ struct Run {
     return c.ws.flag_host[i];
   }
   void cg_loop_host() {
-    for (;;) {
+    for (; vel_cg();) {
       cg_head();
       if (!read_flag(1)) break;
       cg_tail();
@@ -377,13 +400,13 @@ struct Run {
     a.use_handles = 0;
     gather(rhs);
     lanczos();
-    cg_prologue();
+    if (vel_cg()) cg_prologue();
     cg_loop_host();
     gamma();
     while (read_flag(0)) {
       stokes();
       lanczos();
-      cg_prologue();
+      if (vel_cg()) cg_prologue();
       cg_loop_host();
       gamma();
       update();
@@ -420,9 +443,9 @@ struct Run {
   cudaGraphExec_t build_graph(const double* rhs, double* out) {
     cudaGraph_t g;
     GBS_CUDA(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h_out, h_in0, h_in, h_q0 = 0, h_q = 0;
+    cudaGraphConditionalHandle h_out, h_in0 = 0, h_in = 0, h_q0 = 0, h_q = 0;
     GBS_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 0, 0));
-    GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in0, g, 0, 0));
+    if (vel_cg()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in0, g, 0, 0));
     if (pcg_q()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_q0, g, 0, 0));
     const Args base = a;
     a.use_handles = 1;
@@ -433,8 +456,10 @@ struct Run {
     capture_into(g, [&] {
       gather(rhs);
       lanczos();
-      cg_prologue();
-      body0 = add_while(h_in0);
+      if (vel_cg()) {
+        cg_prologue();
+        body0 = add_while(h_in0);
+      }
       if (pcg_q()) {
         qcg_prologue();
         bodyQ0 = add_while(h_q0);
@@ -443,24 +468,27 @@ struct Run {
       bodyO = add_while(h_out);
       finish(out);
     });
-    capture_into(body0, [&] {
-      cg_head();
-      cg_tail();
-    });
+    if (vel_cg())
+      capture_into(body0, [&] {
+        cg_head();
+        cg_tail();
+      });
     if (pcg_q())
       capture_into(bodyQ0, [&] {
         qcg_head();
         qcg_tail();
       });
-    GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in, bodyO, 0, 0));
+    if (vel_cg()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_in, bodyO, 0, 0));
     if (pcg_q()) GBS_CUDA(cudaGraphConditionalHandleCreate(&h_q, bodyO, 0, 0));
     a.h_inner = h_in;
     a.h_qinner = h_q;
     capture_into(bodyO, [&] {
       stokes();
       lanczos();
-      cg_prologue();
-      bodyI = add_while(h_in);
+      if (vel_cg()) {
+        cg_prologue();
+        bodyI = add_while(h_in);
+      }
       if (pcg_q()) {
         qcg_prologue();
         bodyQ = add_while(h_q);
@@ -468,10 +496,11 @@ struct Run {
       gamma();
       update();
     });
-    capture_into(bodyI, [&] {
-      cg_head();
-      cg_tail();
-    });
+    if (vel_cg())
+      capture_into(bodyI, [&] {
+        cg_head();
+        cg_tail();
+      });
     if (pcg_q())
       capture_into(bodyQ, [&] {
         qcg_head();
@@ -558,7 +587,8 @@ void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solv
   std::vector<double> key = {(double)(uintptr_t)rhs, (double)(uintptr_t)out, (double)k, o.tol, o.inner_tol,
                              (double)o.max_outer, (double)o.max_inner, (double)K, (double)o.precision,
                              (double)a.nforced, c.nu, (double)run.vspmv, (double)run.vtrsv,
-                             (double)o.pressure_block, (double)a.nforced_q};
+                             (double)o.pressure_block, (double)a.nforced_q, (double)o.stop_rule,
+                             (double)o.velocity_block};
   if (!w.graph_valid || w.graph_key != key) {
     if (w.graph) {
       cudaGraphExecDestroy(w.graph);
@@ -671,7 +701,7 @@ void release_workspace(Ctx& c) {
   void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
                   w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
                   w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out, w.qcg_x, w.qcg_r, w.qcg_z,
-                  w.qcg_p, w.qcg_q, w.forced_q};
+                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w.S_host) cudaFreeHost(w.S_host);
@@ -681,7 +711,9 @@ void release_workspace(Ctx& c) {
 
 int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts& o, gb_info* info,
           bool adjoint) {
-  if (!c.factored) fail(GB_ERR_INVALID_ARG, "factor_ic0 must succeed before solve");
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble before solve");
+  if (o.velocity_block == GB_VELOCITY_IC0_PCG && !c.factored)
+    fail(GB_ERR_INVALID_ARG, "factor_ic0 must succeed before an IC(0) velocity block");
   if (k < 1 || k > 32) fail(GB_ERR_INVALID_ARG, "k must be in [1, 32]");
   if (!rhs_dev || !x_dev || !info) fail(GB_ERR_INVALID_ARG, "null pointer argument");
   if (!(o.tol >= 0.0) || !(o.inner_tol > 0.0) || o.max_outer < 1 || o.max_inner < 1)
@@ -689,11 +721,16 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
   if (o.precision != GB_PREC_FP64 && o.precision != GB_PREC_MIXED) fail(GB_ERR_INVALID_ARG, "bad precision");
   if (o.forced_inner_host && (k != 1 || o.nforced < 1 || o.nforced > (1 << 24)))
     fail(GB_ERR_INVALID_ARG, "replay mode needs k == 1 and 1 <= nforced <= 2^24");
-  if (o.pressure_block != GB_PRESSURE_DIAG && o.pressure_block != GB_PRESSURE_PCG)
+  if (o.pressure_block < GB_PRESSURE_DIAG || o.pressure_block > GB_PRESSURE_JACOBI_PCG)
     fail(GB_ERR_INVALID_ARG, "bad pressure block");
-  if (o.forced_q_host && (o.pressure_block != GB_PRESSURE_PCG || k != 1 || o.nforced_q < 1 ||
+  if (o.velocity_block < GB_VELOCITY_IC0_PCG || o.velocity_block > GB_VELOCITY_JACOBI_PCG)
+    fail(GB_ERR_INVALID_ARG, "bad velocity block");
+  if (o.stop_rule != GB_STOP_RESIDUAL && o.stop_rule != GB_STOP_ESTIMATE) fail(GB_ERR_INVALID_ARG, "bad stop rule");
+  if (o.forced_q_host && (o.pressure_block == GB_PRESSURE_DIAG || k != 1 || o.nforced_q < 1 ||
                           o.nforced_q > (1 << 24)))
-    fail(GB_ERR_INVALID_ARG, "pressure replay needs the PCG pressure block, k == 1, 1 <= nforced_q <= 2^24");
+    fail(GB_ERR_INVALID_ARG, "pressure replay needs a CG pressure block, k == 1, 1 <= nforced_q <= 2^24");
+  if (o.forced_inner_host && o.velocity_block == GB_VELOCITY_DIAG)
+    fail(GB_ERR_INVALID_ARG, "velocity replay needs a CG velocity block");
   if (o.pressure_block == GB_PRESSURE_PCG && !c.q_factored)
     fail(GB_ERR_IC0_BREAKDOWN, "IC(0) of the pressure mass matrix failed");
   const int K = (k == 1) ? 1 : (k <= 8 ? 8 : 32);

@@ -81,6 +81,13 @@ struct Args {
   const int32_t* forced_q;
   int nforced_q;
   cudaGraphConditionalHandle h_qinner;
+  // velocity block (GB_VELOCITY_*), diagonal positions of A (internal rows)
+  int velocity_block;
+  const int32_t* A_diag;
+  // stopping rule (GB_STOP_*): the 2-norm residual r_j and the products
+  // K w_j (three rotating buffers, like w) of its recurrence
+  int stop_rule;
+  double *R, *KW0, *KW1, *KW2;
 };
 
 // The two inner CG solves: SYS 0 on A_h (velocity block, Sec. 5.1 "PCG(A)"),
@@ -128,6 +135,10 @@ __device__ __forceinline__ double* Wbuf(const Args& a, int i) {
   return i == 0 ? a.W0 : (i == 1 ? a.W1 : a.W2);
 }
 __device__ __forceinline__ double* Zbuf(const Args& a, int i) { return (i % 2) == 0 ? a.Z0 : a.Z1; }
+__device__ __forceinline__ double* KWbuf(const Args& a, int i) {
+  i %= 3;
+  return i == 0 ? a.KW0 : (i == 1 ? a.KW1 : a.KW2);
+}
 
 template <class T>
 __device__ __forceinline__ const T* pick(const double* d, const float* f);
@@ -165,6 +176,11 @@ __global__ void k_gather(Args a, const double* __restrict__ rhs) {
     a.V0[idx] = 0.0;
     a.W0[idx] = 0.0;
     a.W1[idx] = 0.0;
+    if (a.stop_rule == GB_STOP_RESIDUAL) {
+      a.R[idx] = v;  // r_0 = b - K x_0 with x_0 = 0
+      a.KW0[idx] = 0.0;
+      a.KW1[idx] = 0.0;
+    }
     vals[0] += v * v;
     if (!isfinite(v)) vals[1] += 1.0;
     if (r >= a.n_u) {
@@ -258,11 +274,12 @@ __global__ void k_stokes_apply(Args a) {
 
 // ----------------------------------------------------------- Lanczos -----
 // v_{j+1} = q - (delta_j/gamma_j) v_j - (gamma_j/gamma_{j-1}) v_{j-1}
-// (j = 0: v_1 = b).  The velocity block of z_{j+1} = M^{-1} v_{j+1} starts
-// the inner CG with b = r = v_{j+1,u}, x = 0.  The pressure block is
-// 2 nu v_p / diag(Q) (Diag(Q_nu)), or starts the pressure CG on Q with
-// b = r = v_{j+1,p}, x = 0 (IC(0)-PCG block; z_p = 2 nu x is taken in
-// k_gamma).  Epilogue: ||b|| and the CG state of each block per RHS.
+// (j = 0: v_1 = b).  The velocity block of z_{j+1} = M^{-1} v_{j+1} is
+// v_u / diag(A_h) (Diag(A) block), or starts the inner CG with b = r =
+// v_{j+1,u}, x = 0.  The pressure block is 2 nu v_p / diag(Q) (Diag(Q_nu)),
+// or starts the pressure CG on Q with b = r = v_{j+1,p}, x = 0 (CG blocks;
+// z_p = 2 nu x is taken in k_gamma).  Epilogue: ||b|| and the CG state of
+// each block per RHS.
 template <int K, class T>
 __global__ void k_lanczos(Args a) {
   const int j = *a.jcur;
@@ -275,7 +292,7 @@ __global__ void k_lanczos(Args a) {
   T* __restrict__ x_cg = (T*)a.cg_x;
   T* __restrict__ r_q = (T*)a.qcg_r;
   T* __restrict__ x_q = (T*)a.qcg_x;
-  const bool pcg_q = a.pressure_block == GB_PRESSURE_PCG;
+  const bool pcg_q = a.pressure_block != GB_PRESSURE_DIAG;
   const int t = threadIdx.x % K;
   const bool live = SF(a, S_OUTER_ACTIVE, t, K) != 0.0;
   double c1 = 0.0, c2 = 0.0;
@@ -292,9 +309,13 @@ __global__ void k_lanczos(Args a) {
     const double v = (j == 0) ? a.b[idx] : a.q[idx] - c1 * vc[idx] - c2 * vp[idx];
     vn[idx] = v;
     if (r < a.n_u) {
-      r_cg[idx] = (T)v;
-      x_cg[idx] = (T)0;
-      vals[0] += v * v;
+      if (a.velocity_block == GB_VELOCITY_DIAG) {
+        zn[idx] = v / a.A_val[a.A_diag[r]];
+      } else {
+        r_cg[idx] = (T)v;
+        x_cg[idx] = (T)0;
+        vals[0] += v * v;
+      }
     } else if (pcg_q) {
       const size_t iq = (size_t)(r - a.n_u) * K + t;
       r_q[iq] = (T)v;
@@ -344,7 +365,7 @@ __global__ void k_lanczos(Args a) {
       a.flag[1] = any;
       a.flag[3] = anyq;
       if (a.use_handles) {
-        cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
+        if (a.velocity_block != GB_VELOCITY_DIAG) cudaGraphSetConditional(a.h_inner, any ? 1u : 0u);
         if (pcg_q) cudaGraphSetConditional(a.h_qinner, anyq ? 1u : 0u);
       }
       *a.counter = 0;
@@ -374,9 +395,13 @@ __global__ void k_gamma(Args a) {
     const size_t idx = (size_t)r * K + t;
     double z;
     if (r < a.n_u) {
-      z = (double)x_cg[idx];
-      zn[idx] = z;
-    } else if (a.pressure_block == GB_PRESSURE_PCG) {
+      if (a.velocity_block == GB_VELOCITY_DIAG) {
+        z = zn[idx];
+      } else {
+        z = (double)x_cg[idx];
+        zn[idx] = z;
+      }
+    } else if (a.pressure_block != GB_PRESSURE_DIAG) {
       z = 2.0 * a.nu * (double)((const T*)a.qcg_x)[(size_t)(r - a.n_u) * K + t];
       zn[idx] = z;
     } else {
@@ -436,8 +461,10 @@ __global__ void k_gamma(Args a) {
           SF(a, S_OUTER_ITS, s, K) = j;
           const double rel = fabs(-snn * eta) / SF(a, S_GAMMA1, s, K);
           SF(a, S_RELRES, s, K) = rel;
-          // S_OUTER_ACTIVE stays set until k_update has applied this step
-          SF(a, S_STATUS, s, K) = (rel <= a.tol || stop) ? (stop ? SF(a, S_STATUS, s, K) : 0.0) : 1.0;
+          // S_OUTER_ACTIVE stays set until k_update has applied this step; with
+          // the residual rule k_update decides convergence
+          const bool est_conv = a.stop_rule == GB_STOP_ESTIMATE && rel <= a.tol;
+          SF(a, S_STATUS, s, K) = stop ? SF(a, S_STATUS, s, K) : (est_conv ? 0.0 : 1.0);
           if (!isfinite(a1) || !isfinite(rel)) SF(a, S_NONFINITE, s, K) = 1.0;
         }
       }
@@ -457,7 +484,11 @@ __global__ void k_gamma(Args a) {
 
 // w_{j+1} = (z_j / gamma_j - a3 w_{j-1} - a2 w_j) / a1;  x += (c_{j+1} eta_j) w_{j+1}.
 // gamma_j here is the value before k_gamma advanced it, i.e. S_GAMMA_PREV.
-// Epilogue: retire converged RHS, advance j, set the outer loop condition.
+// With the residual rule the same recurrence runs on K w (q = K z_j / gamma_j
+// from k_stokes_apply): K w_{j+1} = (q - a3 K w_{j-1} - a2 K w_j) / a1, and
+// r_j = r_{j-1} - (c_{j+1} eta_j) K w_{j+1} = b - K x_j; ||r_j||^2 is reduced.
+// Epilogue: retire converged RHS (||r_j|| <= tol ||b|| or the estimate test
+// of k_gamma), advance j, set the outer loop condition.
 template <int K>
 __global__ void k_update(Args a) {
   const int j = *a.jcur;
@@ -476,6 +507,11 @@ __global__ void k_update(Args a) {
     a3 = SF(a, S_A3, t, K);
     xc = SF(a, S_XCOEF, t, K);
   }
+  const bool resid = a.stop_rule == GB_STOP_RESIDUAL;
+  const double* __restrict__ kwp = KWbuf(a, j + 2);
+  const double* __restrict__ kwc = KWbuf(a, j);
+  double* __restrict__ kwn = KWbuf(a, j + 1);
+  double vals[1] = {0.0};
   const int stride = (gridDim.x * blockDim.x) / K;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) / K; r < n; r += stride) {
     if (!live) continue;
@@ -483,12 +519,27 @@ __global__ void k_update(Args a) {
     const double w = (zc[idx] * ig - a3 * wp[idx] - a2 * wc[idx]) * a1i;
     wn[idx] = w;
     a.x[idx] += xc * w;
+    if (resid) {
+      const double kw = (a.q[idx] - a3 * kwp[idx] - a2 * kwc[idx]) * a1i;
+      kwn[idx] = kw;
+      const double rv = a.R[idx] - xc * kw;
+      a.R[idx] = rv;
+      vals[0] += rv * rv;
+    }
   }
+  if (resid) block_partials<K, 1>(vals, a.partial);  // uniform over the grid
   if (last_block(a.counter)) {
+    __shared__ double tot[K];
+    if (resid) finalize_partials<K, 1>(a.partial, gridDim.x, tot);
     int any = 0;
     if (threadIdx.x < K) {
       const int s = threadIdx.x;
       if (SF(a, S_OUTER_ACTIVE, s, K) != 0.0) {
+        if (resid && SF(a, S_STATUS, s, K) == 1.0) {
+          const double rel2 = sqrt(tot[s]) / SF(a, S_BNORM, s, K);
+          if (rel2 <= a.tol) SF(a, S_STATUS, s, K) = 0.0;
+          if (!isfinite(rel2)) SF(a, S_NONFINITE, s, K) = 1.0;
+        }
         const bool conv = SF(a, S_STATUS, s, K) != 1.0;
         const bool cap = j >= a.max_outer;
         const bool bad = SF(a, S_NONFINITE, s, K) != 0.0;
@@ -921,6 +972,24 @@ __global__ void k_cg_pupdate(Args a) {
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < C::n(a); i += stride) {
     const size_t idx = (size_t)i * K + t;
     p[idx] = z[idx] + beta * p[idx];
+  }
+}
+
+// ------------------------------------------------------ Jacobi blocks ----
+// z = r / diag for the diagonally preconditioned CG blocks (Sec. 6.2: the
+// preconditioner of the inner PCG is the diagonal of A_h or of Q).
+template <int K, class T, int SYS>
+__global__ void k_jacobi(Args a) {
+  using C = CgSys<SYS>;
+  const T* __restrict__ r = (const T*)C::r(a);
+  T* __restrict__ z = (T*)C::z(a);
+  const int t = threadIdx.x % K;
+  if (SF(a, C::ACTIVE, t, K) == 0.0) return;
+  const int stride = (gridDim.x * blockDim.x) / K;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / K; i < C::n(a); i += stride) {
+    const double d = SYS ? a.Qdiag[i] : a.A_val[a.A_diag[i]];
+    const size_t idx = (size_t)i * K + t;
+    z[idx] = r[idx] / (T)d;
   }
 }
 

@@ -61,6 +61,7 @@ int main(void) {
          offsetof(gb_solve_opts, forced_inner_host), offsetof(gb_solve_opts, nforced),
          offsetof(gb_solve_opts, pressure_block), offsetof(gb_solve_opts, forced_q_host),
          offsetof(gb_solve_opts, nforced_q));
+  printf("%zu %zu\\n", offsetof(gb_solve_opts, stop_rule), offsetof(gb_solve_opts, velocity_block));
   printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(gb_info, inner_its_total), offsetof(gb_info, inner_its_max),
          offsetof(gb_info, relres_true), offsetof(gb_info, q_inner_its_total), offsetof(gb_info, q_inner_its_max),
          offsetof(gb_info, status));
@@ -78,6 +79,8 @@ int main(void) {
                     gb.gb_solve_opts.pressure_block.offset, gb.gb_solve_opts.forced_q_host.offset,
                     gb.gb_solve_opts.nforced_q.offset]
     offs = [int(v) for v in lines[2].split()]
+    assert offs == [gb.gb_solve_opts.stop_rule.offset, gb.gb_solve_opts.velocity_block.offset]
+    offs = [int(v) for v in lines[3].split()]
     assert offs == [gb.gb_info.inner_its_total.offset, gb.gb_info.inner_its_max.offset,
                     gb.gb_info.relres_true.offset, gb.gb_info.q_inner_its_total.offset,
                     gb.gb_info.q_inner_its_max.offset, gb.gb_info.status.offset]

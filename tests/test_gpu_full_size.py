@@ -109,13 +109,14 @@ def test_full_size_solution_properties(oracle_mod, gb, name, precision):
     s = problem(gb, name)
     rhs = _rhs(s, 1, 0)[0]
     x, info = s.solve(rhs, tol=1e-8, inner_tol=1e-2, precision=precision)
-    assert info["status"] == 0 and info["relres_est"] <= 1e-8
+    assert info["status"] == 0
     b = rhs.cpu().numpy()
     xv = x.cpu().numpy()
     r = b - s.apply("K", x).cpu().numpy()
     relres = np.linalg.norm(r) / np.linalg.norm(b)
     assert abs(relres - info["relres_true"]) <= 1e-3 * relres + 1e-15
-    assert relres <= 1e-6
+    # the 2-norm stopping rule (carried by a recurrence on the device)
+    assert relres <= 1.01e-8
     # the residual on sampled rows, from the oracle's own rows of A_h and B
     ref, ru, rp = sampled_oracle(oracle_mod, s, seed=2)
     xu, xp = xv[: s.n_u], xv[s.n_u:]
@@ -138,17 +139,17 @@ def test_full_size_3d48_batched_and_adjoint(gb):
     u(nu) = u(1) / nu and dL/dnu = -(u - u_t)^T u / nu exactly (the oracle
     test of the adjoint pins the same identity at small size). The batch stops
     at 1e-6: with the diagonal pressure block and a relaxed inner solve, some
-    3D forcings stall near 1e-8 in the |eta| / gamma_1 estimate for thousands
-    of steps while their 2-norm residual is already an order lower."""
+    3D forcings need thousands of steps to 1e-8 (and stall in the
+    |eta| / gamma_1 estimate while their 2-norm residual is an order lower)."""
     from paper_1309_5048_gb300.inputs import target_velocity
     s = problem(gb, "3d48")
     R = _rhs(s, 32, 0)
     X, infos = s.solve(R, tol=1e-6, inner_tol=1e-2, precision="mixed")
-    assert all(i["status"] == 0 and i["relres_est"] <= 1e-6 for i in infos)
+    assert all(i["status"] == 0 and i["relres_true"] <= 1.01e-6 for i in infos)
     for t in (0, 13, 31):
         r = R[t] - s.apply("K", X[t])
         rel = float(r.norm() / R[t].norm())
-        assert rel <= 1e-4
+        assert rel <= 1.01e-6
         assert abs(rel - infos[t]["relres_true"]) <= 1e-3 * rel
     # adjoint of one column, FP64 solves: dL/dnu = -lambda_u^T A_0 u
     x0, i0 = s.solve(R[1], tol=1e-9, inner_tol=1e-2)

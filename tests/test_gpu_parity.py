@@ -156,8 +156,7 @@ def test_solve_free_mode(oracle_mod, gb, precision, ordering):
     xr, ir = ref.minres(b, tol=1e-8, inner_tol=1e-2)
     x, info = s.solve(rhs, tol=1e-8, inner_tol=1e-2, precision=precision)
     x = x.cpu().numpy()
-    assert info["status"] == 0 and info["relres_est"] <= 1e-8
-    assert info["relres_true"] <= 1e-6
+    assert info["status"] == 0 and info["relres_true"] <= 1.01e-8
     e_ref = rel(xr, x_tight)
     e_gpu = rel(x, x_tight)
     assert e_gpu <= max(10 * e_ref, 1e-7), (e_gpu, e_ref)
