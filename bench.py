@@ -57,6 +57,8 @@ def parse():
                     help="single-RHS SpMV layout of the benchmark precision (auto: timed at the first solve)")
     ap.add_argument("--trsv", choices=["auto", "csr", "sell", "staged4", "staged12", "staged32"], default="auto",
                     help="single-RHS IC(0) sweep layout of the benchmark precision")
+    ap.add_argument("--stop", choices=["residual", "estimate"], default="residual",
+                    help="MINRES stop: ||b - Kx|| / ||b|| <= tol (the paper's relative residual) or |eta| / gamma_1")
     ap.add_argument("--pressure", choices=["diag", "pcg"], default="diag",
                     help="pressure block: Diag(Q_nu) or IC(0)-PCG on Q_nu (Sec. 6.4)")
     ap.add_argument("--k", type=int, default=1, help="right-hand sides per solve")
@@ -215,7 +217,7 @@ def launches_per_solve(s, info, pressure="diag"):
     return n
 
 
-def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0, pressure="diag"):
+def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0, pressure="diag", stop="residual"):
     """The oracle as it stands, single-threaded, on a bounded sample of one
     solve: the first m MINRES iterations, extrapolated to the full solve."""
     import numpy as np
@@ -228,11 +230,11 @@ def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0, pressur
     kappa, amp = fourier_modes(W["dim"], seed=0)
     b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
     t = time.perf_counter()
-    P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2, pressure=pressure)
+    P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2, pressure=pressure, stop=stop)
     pilot = (time.perf_counter() - t) / 2
     m = int(max(2, min(outer_full, target_s / max(pilot, 1e-6))))
     t = time.perf_counter()
-    _, info = P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=m, pressure=pressure)
+    _, info = P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=m, pressure=pressure, stop=stop)
     dt = time.perf_counter() - t
     per_outer = dt / max(info["outer"], 1)
     est = per_outer * max(outer_full, 1)
@@ -257,7 +259,7 @@ def run_reference(args):
     P.factor_q()
     kappa, amp = fourier_modes(W["dim"], seed=0)
     b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
-    pres = dict(pressure=args.pressure)
+    pres = dict(pressure=args.pressure, stop=args.stop)
     # one untimed full solve gives the outer count used to extrapolate samples
     t = time.perf_counter()
     x, full = P.minres(b, tol=args.tol, inner_tol=args.inner_tol, **pres)
@@ -281,7 +283,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["desc"], "ordering": args.ordering, "k": 1, "tol": args.tol,
                        "inner_tol": args.inner_tol,
-                       "pressure_block": "Diag(Q)" if args.pressure == "diag" else "IC(0)-PCG(Q)"},
+                       "pressure_block": "Diag(Q)" if args.pressure == "diag" else "IC(0)-PCG(Q)",
+                       "stop": args.stop},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "outer_its": outer_full, "relres_true": full["relres_true"]}
@@ -330,7 +333,7 @@ def main():
     rhs = make_rhs(k, rank * 1000)
     out = torch.empty_like(rhs)
     opts = dict(tol=args.tol, inner_tol=args.inner_tol, precision=args.precision, use_graph=not args.no_graph,
-                max_outer=args.max_outer, pressure=args.pressure)
+                max_outer=args.max_outer, pressure=args.pressure, stop=args.stop)
 
     def timed(rhs_, out_, steps, warmup, **o):
         info = None
@@ -413,7 +416,7 @@ def main():
             o = torch.empty_like(r)
             st = 1 if kk > 1 else max(1, args.steps // 2)
             ms_v, inf_v = timed(r, o, st, 1, tol=args.tol, inner_tol=args.inner_tol, precision=prec,
-                                use_graph=not args.no_graph, pressure=pres)
+                                use_graph=not args.no_graph, pressure=pres, stop=args.stop)
             iv = inf_v if isinstance(inf_v, list) else [inf_v]
             variants[name] = {"solves_per_s": st * kk / (ms_v / 1000.0), "k": kk, "precision": prec,
                               "pressure_block": "Diag(Q)" if pres == "diag" else "IC(0)-PCG(Q)",
@@ -424,7 +427,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(W, args.ordering, args.tol, args.inner_tol, int(infos[0]["outer_its"]),
-                           pressure=args.pressure)
+                           pressure=args.pressure, stop=args.stop)
 
     if rank == 0:
         line = {
@@ -434,6 +437,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": W["desc"], "ordering": args.ordering, "k": k, "precision": args.precision,
                        "pressure_block": "Diag(Q)" if args.pressure == "diag" else "IC(0)-PCG(Q)",
+                       "stop": ("||b - K x||_2 / ||b||_2 <= tol" if args.stop == "residual"
+                                else "|eta| / gamma_1 <= tol"),
                        "tol": args.tol, "inner_tol": args.inner_tol, "graph": not args.no_graph,
                        "l2": "no flush: per-iteration working set (A, L, L^T, vectors) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
