@@ -41,6 +41,10 @@ WORKLOADS = {
     "3d32": dict(dim=3, N=32, p=3, desc="3D unit cube, 32^3 elements, k'=2, nu=1, 16-mode Fourier forcing"),
     "2d1024": dict(dim=2, N=1024, p=3, desc="2D unit square, 1024x1024 elements, k'=2, nu=1, Fourier forcing"),
     "3d48": dict(dim=3, N=48, p=3, desc="3D unit cube, 48^3 elements, k'=2, nu=1, Fourier forcing"),
+    # the paper's own benchmark problem (Sec. 6.4); run it as in Table ic_pgc_tols_k2 with
+    # --pressure pcg --tol 1e-12 --inner-tol 1e-3
+    "cavity256": dict(dim=2, N=256, p=3, load="cavity",
+                      desc="2D lid-driven cavity, 256x256 elements, k'=2, nu=1, unit lid velocity (Nitsche load)"),
 }
 
 
@@ -217,18 +221,25 @@ def launches_per_solve(s, info, pressure="diag"):
     return n
 
 
+def oracle_load(P, W):
+    """The workload's load vector from the oracle (forcing seed 0)."""
+    from paper_1309_5048_gb300.inputs import fourier_modes
+    if W.get("load") == "cavity":
+        return P.load_cavity()
+    kappa, amp = fourier_modes(W["dim"], seed=0)
+    return P.load_fourier(kappa, amp)
+
+
 def cpu_baseline(W, ordering, tol, inner_tol, outer_full, target_s=15.0, pressure="diag", stop="residual"):
     """The oracle as it stands, single-threaded, on a bounded sample of one
     solve: the first m MINRES iterations, extrapolated to the full solve."""
     import numpy as np
 
     import oracle
-    from paper_1309_5048_gb300.inputs import fourier_modes
     P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=ordering)
     P.factor()
     P.factor_q()
-    kappa, amp = fourier_modes(W["dim"], seed=0)
-    b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
+    b = np.concatenate([oracle_load(P, W), np.zeros(P.n_p)])
     t = time.perf_counter()
     P.minres(b, tol=tol, inner_tol=inner_tol, max_outer=2, pressure=pressure, stop=stop)
     pilot = (time.perf_counter() - t) / 2
@@ -252,13 +263,11 @@ def run_reference(args):
     import numpy as np
 
     import oracle
-    from paper_1309_5048_gb300.inputs import fourier_modes
     W = WORKLOADS[args.workload]
     P = oracle.Problem(W["dim"], W["N"], W["p"], ordering=args.ordering)
     P.factor()
     P.factor_q()
-    kappa, amp = fourier_modes(W["dim"], seed=0)
-    b = np.concatenate([P.load_fourier(kappa, amp), np.zeros(P.n_p)])
+    b = np.concatenate([oracle_load(P, W), np.zeros(P.n_p)])
     pres = dict(pressure=args.pressure, stop=args.stop)
     # one untimed full solve gives the outer count used to extrapolate samples
     t = time.perf_counter()
@@ -326,8 +335,11 @@ def main():
     def make_rhs(k, seed0):
         rhs = torch.zeros(k, s.n, dtype=torch.float64, device="cuda")
         for t in range(k):
-            kap, amp = fourier_modes(W["dim"], seed=seed0 + t)
-            rhs[t, : s.n_u] = s.load_fourier(kap, amp)
+            if W.get("load") == "cavity":  # column t: lid speed 1 + t + seed0 / 1000
+                rhs[t, : s.n_u] = s.load_cavity() * (1.0 + t + seed0 / 1000.0)
+            else:
+                kap, amp = fourier_modes(W["dim"], seed=seed0 + t)
+                rhs[t, : s.n_u] = s.load_fourier(kap, amp)
         return rhs
 
     rhs = make_rhs(k, rank * 1000)

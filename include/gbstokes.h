@@ -176,6 +176,13 @@ int gb_load_fourier(gb_ctx* ctx, int nmodes, const int32_t* kappa_host,
  * (eq. manufactured_force), with the nu of the last gb_assemble. */
 int gb_load_manufactured(gb_ctx* ctx, double* f_dev);
 
+/* Load of the lid-driven cavity (Sec. 6.4): no body force, and the Nitsche
+ * right-hand side l_h of eq. nitsche_rhs with lid velocity g = e_1 on the
+ * face x_dim = 1 (y = 1 in 2D), g = 0 elsewhere, with the nu and C_pen of the
+ * last gb_assemble.  f_dev: n_u doubles, natural numbering (the pressure part
+ * of the right-hand side is zero). */
+int gb_load_cavity(gb_ctx* ctx, double* f_dev);
+
 /* IC(0) of the permuted A_h (Sec. 6.4): L L^T = A on the pattern of L, no
  * fill, FP64, level-scheduled on the device; also builds the FP32 copies used
  * by GB_PREC_MIXED.  On GB_ERR_IC0_BREAKDOWN *breakdown_row_host (may be NULL)

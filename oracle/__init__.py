@@ -59,7 +59,7 @@ def lib():
             L.or_create.argtypes = [i32, i32, i32, dbl, dbl, i32, i32, vp, vp]
             L.or_destroy.argtypes = [vp]
             for name in ("or_sizes", "or_csr", "or_wmean", "or_perm", "or_load_fourier",
-                         "or_load_manufactured", "or_manufactured_errors", "or_minres",
+                         "or_load_manufactured", "or_manufactured_errors", "or_minres", "or_load_cavity",
                          "or_pcg", "or_precond", "or_stokes_apply", "or_filter", "or_perm_q",
                          "or_pcg_q"):
                 getattr(L, name).restype = i32
@@ -74,6 +74,7 @@ def lib():
             L.or_factor_q.argtypes = [vp]
             L.or_load_fourier.argtypes = [vp, i32, vp, vp, vp]
             L.or_load_manufactured.argtypes = [vp, vp]
+            L.or_load_cavity.argtypes = [vp, vp]
             L.or_manufactured_errors.argtypes = [vp, vp, vp, vp]
             L.or_manufactured_point.argtypes = [dbl, dbl, dbl, vp]
             L.or_minres.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, vp, i64, i32, vp, i64, i32, i32, vp]
@@ -221,6 +222,14 @@ class Problem:
     def load_manufactured(self):
         f = np.zeros(self.n_u)
         if lib().or_load_manufactured(self._h, _p(f)) != 0:
+            raise RuntimeError(lib().or_last_error().decode())
+        return f
+
+    def load_cavity(self):
+        """Lid-driven cavity load (Sec. 6.4): the Nitsche right-hand side of
+        eq. nitsche_rhs with lid velocity e_1 on x_dim = 1 (velocity part)."""
+        f = np.zeros(self.n_u)
+        if lib().or_load_cavity(self._h, _p(f)) != 0:
             raise RuntimeError(lib().or_last_error().decode())
         return f
 

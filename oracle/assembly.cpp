@@ -516,6 +516,71 @@ static Manu manu_eval(double nu, double x, double y) {
   return m;
 }
 
+// Lid-driven cavity load (Sec. 6.4): no body force, and the Nitsche
+// right-hand side of eq. nitsche_rhs,
+//   l_h(v) = sum_F int_F 2 nu ( -((grad^s v) n) . g + (C_pen / h_F) g . v ) dS,
+// with the lid velocity g = e_1 on the face x_dim = 1 and g = 0 on the other
+// faces.  Gauss quadrature with p+1 points per direction on the lid faces.
+void load_cavity(const Problem& P, std::vector<double>& f) {
+  f.assign(P.n_u, 0.0);
+  const int dim = P.dim, N = P.N, p = P.p, ng = p + 1;
+  const Table1D T[2] = {make_table(P.Kp, ng), make_table(P.Kq, ng)};
+  const double hF = 1.0 / N;
+  const int k = dim - 1;  // lid normal direction
+  double nrm[3] = {0, 0, 0}, gl[3] = {1.0, 0, 0};
+  nrm[k] = 1.0;
+  double fv[2][16], fd[2][16];
+  eval_basis(P.Kp, N - 1, 1.0, fv[0], fd[0]);
+  eval_basis(P.Kq, N - 1, 1.0, fv[1], fd[1]);
+  std::vector<LocalFun> vf;
+  int64_t nface = 1;  // elements of the lid face
+  for (int m = 0; m < dim; ++m)
+    if (m != k) nface *= N;
+  for (int64_t fe = 0; fe < nface; ++fe) {
+    int e[3] = {0, 0, 0};
+    int64_t rest = fe;
+    for (int m = 0; m < dim; ++m) {
+      if (m == k) {
+        e[m] = N - 1;
+      } else {
+        e[m] = (int)(rest % N);
+        rest /= N;
+      }
+    }
+    element_vfuns(P, e, vf);
+    int gq[3] = {0, 0, 0};
+    for (gq[0] = 0; gq[0] < (k == 0 ? 1 : ng); ++gq[0])
+      for (gq[1] = 0; gq[1] < (k == 1 ? 1 : ng); ++gq[1])
+        for (gq[2] = 0; gq[2] < ((dim == 3 && k != 2) ? ng : 1); ++gq[2]) {
+          double w = 1.0;
+          for (int m = 0; m < dim; ++m)
+            if (m != k) w *= T[0].w[(size_t)e[m] * ng + gq[m]];
+          for (const LocalFun& fn : vf) {
+            double v1[3], d1[3];
+            for (int m = 0; m < dim; ++m) {
+              const int sel = P.deg(fn.comp, m) == p ? 0 : 1;
+              v1[m] = (m == k) ? fv[sel][fn.off[m]] : T[sel].v(e[m], gq[m], fn.off[m]);
+              d1[m] = (m == k) ? fd[sel][fn.off[m]] : T[sel].d(e[m], gq[m], fn.off[m]);
+            }
+            double val = 1.0, grad[3] = {0, 0, 0};
+            for (int m = 0; m < dim; ++m) val *= v1[m];
+            for (int m = 0; m < dim; ++m) {
+              grad[m] = d1[m];
+              for (int mm = 0; mm < dim; ++mm)
+                if (mm != m) grad[m] *= v1[mm];
+            }
+            double S[3][3];
+            sym_grad(dim, fn.comp, grad, S);
+            double tg = 0.0;  // ((grad^s Phi) n) . g
+            for (int r = 0; r < dim; ++r)
+              for (int c = 0; c < dim; ++c) tg += gl[r] * S[r][c] * nrm[c];
+            const double phig = val * gl[fn.comp];
+            f[fn.gidx] += w * 2.0 * P.nu * (-tg + (P.cpen / hF) * phig);
+          }
+        }
+  }
+}
+
 void manufactured_point(double nu, double x, double y, double out[5]) {
   Manu m = manu_eval(nu, x, y);
   out[0] = m.u[0];

@@ -183,6 +183,12 @@ int or_load_manufactured(void* hv, double* f) {
          std::memcpy(f, v.data(), sizeof(double) * v.size()); return 0;)
 }
 
+int or_load_cavity(void* hv, double* f) {
+  Handle* h = static_cast<Handle*>(hv);
+  OR_TRY(std::vector<double> v; load_cavity(h->P, v);
+         std::memcpy(f, v.data(), sizeof(double) * v.size()); return 0;)
+}
+
 int or_manufactured_errors(void* hv, const double* u, const double* p, double* out) {
   Handle* h = static_cast<Handle*>(hv);
   OR_TRY(manufactured_errors(h->P, u, p, out); return 0;)

@@ -87,6 +87,9 @@ void load_fourier(const Problem& P, int nmodes, const int* kappa, const double* 
                   std::vector<double>& f);
 // Load vector for the Sec. 6.2 manufactured solution (2D only).
 void load_manufactured(const Problem& P, std::vector<double>& f);
+// Lid-driven cavity (Sec. 6.4): f = 0 and the Nitsche load l_h of
+// eq. nitsche_rhs with lid velocity e_1 on the face x_dim = 1.
+void load_cavity(const Problem& P, std::vector<double>& f);
 // Errors |u-u_h|_{H1}, ||u-u_h||_{L2}, ||p-p_h||_{L2} for Sec. 6.2 (2D only).
 void manufactured_errors(const Problem& P, const double* u, const double* p, double out[3]);
 // Exact manufactured fields at (x,y): u1,u2,p,f1,f2 (for pinning).

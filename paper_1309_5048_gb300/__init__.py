@@ -59,7 +59,7 @@ class gb_info(C.Structure):
 EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
             "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel",
-            "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc"]
+            "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc", "gb_load_cavity"]
 
 
 def library_path() -> str:
@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
         L.gb_assemble.argtypes = [vp, dbl, dbl]
         L.gb_load_fourier.argtypes = [vp, i32, vp, vp, vp]
         L.gb_load_manufactured.argtypes = [vp, vp]
+        L.gb_load_cavity.argtypes = [vp, vp]
         L.gb_factor_ic0.argtypes = [vp, C.POINTER(i64)]
         L.gb_solve.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_solve_host.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
@@ -177,6 +178,13 @@ class Stokes:
     def load_manufactured(self):
         f = self.torch.empty(self.n_u, dtype=self.torch.float64, device=self.device)
         _check(load_library().gb_load_manufactured(self._h, _ptr(f)))
+        return f
+
+    def load_cavity(self):
+        """Lid-driven cavity load (Sec. 6.4): the Nitsche right-hand side with
+        lid velocity e_1 on x_dim = 1 (velocity part, natural numbering)."""
+        f = self.torch.empty(self.n_u, dtype=self.torch.float64, device=self.device)
+        _check(load_library().gb_load_cavity(self._h, _ptr(f)))
         return f
 
     def factor_ic0(self):

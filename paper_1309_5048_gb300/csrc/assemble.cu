@@ -491,6 +491,36 @@ __global__ void k_manufactured_load(SpaceDev Sp, Rule rule, double nu, double* _
   }
 }
 
+// Lid-driven cavity load (Sec. 6.4): the Nitsche right-hand side of
+// eq. nitsche_rhs with lid velocity g = e_1 on the face x_k = 1, k = dim - 1.
+// Only the first velocity component has a tangential trace along e_1 there:
+// for Phi = phi e_1, ((grad^s Phi) n) . g = (1/2) d_k phi, so
+//   l = 2 nu prod_{m != k} (int_0^1 B_{a_m}) * (-(1/2) B'_{a_k}(1) + (C_pen / h_F) B_{a_k}(1)),
+// with int_0^1 B^q_a = (xi_{a+q+1} - xi_a) / (q+1) and the end values from
+// Cox-de Boor on the last element.  Other components give 0 (their normal
+// trace on the lid is removed from the space, so phi = d_1 phi = 0 there).
+__global__ void k_cavity_load(SpaceDev Sp, double nu, double cpen, double* __restrict__ f, int n_u) {
+  const int N = Sp.N, p = Sp.p, k = Sp.dim - 1;
+  double v[8], d[8];
+  bspline_element(N, p - 1, N - 1, 1.0, v, d);  // degree p-1 functions N-1 .. N+p-2 at x = 1
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += gridDim.x * blockDim.x) {
+    int c, a[3] = {0, 0, 0};
+    vdecode_dev(Sp, i, &c, a);
+    double out = 0.0;
+    if (c == 0 && a[k] >= N - 1) {
+      const int t = a[k] - (N - 1);
+      double w = 1.0;
+      for (int m = 0; m < Sp.dim; ++m) {
+        if (m == k) continue;
+        const int q = (m == 0) ? p : p - 1;  // degree of component 1 in direction m
+        w *= (open_knot(a[m] + q + 1, q, N) - open_knot(a[m], q, N)) / (q + 1);
+      }
+      out = 2.0 * nu * w * (-0.5 * d[t] + cpen * N * v[t]);
+    }
+    f[i] = out;
+  }
+}
+
 int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
@@ -561,6 +591,14 @@ void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, d
   kd.free_();
   ad.free_();
   S.free_();
+}
+
+void load_cavity(Ctx& c, double* f_dev) {
+  if (!c.assembled) fail(GB_ERR_INVALID_ARG, "assemble first (the load uses nu and C_pen)");
+  if (!f_dev) fail(GB_ERR_INVALID_ARG, "null output");
+  k_cavity_load<<<grid_for(c.n_u, 128), 128, 0, c.stream>>>(make_space(c), c.nu, c.cpen, f_dev, (int)c.n_u);
+  GBS_CUDA(cudaGetLastError());
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 void load_manufactured(Ctx& c, double* f_dev) {

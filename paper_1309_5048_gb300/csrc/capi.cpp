@@ -175,6 +175,14 @@ int gb_load_manufactured(gb_ctx* h, double* f_dev) {
   });
 }
 
+int gb_load_cavity(gb_ctx* h, double* f_dev) {
+  if (!h) return GB_ERR_INVALID_ARG;
+  return guarded([&] {
+    StreamOrder order(h->c);
+    load_cavity(h->c, f_dev);
+  });
+}
+
 int gb_factor_ic0(gb_ctx* h, int64_t* breakdown_row_host) {
   if (!h) return GB_ERR_INVALID_ARG;
   int64_t row = -1;

@@ -221,6 +221,7 @@ void setup_pattern(Ctx& c, const gb_problem& prob);
 void assemble(Ctx& c, double nu, double cpen);
 void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, double* f_dev);
 void load_manufactured(Ctx& c, double* f_dev);
+void load_cavity(Ctx& c, double* f_dev);
 // factor.cu
 int64_t factor_ic0(Ctx& c);
 void sell_refill(Ctx& c, Sell& S, const double* csr_val);
