@@ -235,6 +235,24 @@ int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, doubl
  * and result are those of gb_dnu. */
 int gb_dnu_noalloc(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
 
+/* Spectral diagnostics.  MINRES is the Lanczos process on M^{-1} K in the
+ * M-inner product (Sec. 5); after j steps the tridiagonal T_j (diagonal
+ * delta_1..delta_j, off-diagonal gamma_2..gamma_j) represents M^{-1} K on the
+ * Krylov space, and its eigenvalues (Ritz values) approximate eigenvalues of
+ * M^{-1} K, the extremal ones first -- on meshes too large for a dense
+ * eigensolver (the paper's Tables neg_and_pos_eig_k_2/k_3 are dense).
+ * gb_lanczos: T_j of right-hand side `rhs` (0 <= rhs < k) of the last solve;
+ * *count = j; delta_host receives min(j, cap) values delta_1.., gamma_host
+ * min(j+1, cap+1) values gamma_1, gamma_2, .. (gamma_1 = ||b||_{M^{-1}}).
+ * Either pointer may be NULL.  Without a completed solve: GB_ERR_INVALID_ARG.
+ * gb_ritz_extremes: out_host[0..3] = lambda^-_min, lambda^-_max, lambda^+_min,
+ * lambda^+_max of the Ritz values (bisection on Sturm sequences, host);
+ * exclude_one != 0 skips Ritz values within 1e-6 of 1 (the paper discards the
+ * eigenvalue 1, of multiplicity n_u - n_p when M_A = A_h); NaN where a side
+ * has no Ritz value. */
+int gb_lanczos(gb_ctx* ctx, int rhs, double* delta_host, double* gamma_host, int cap, int* count);
+int gb_ritz_extremes(gb_ctx* ctx, int rhs, int exclude_one, double* out_host);
+
 /* y = K x (which = 0), y_u = A_h x_u (which = 1), y_p = B x_u (which = 2),
  * y_u = B^T x_p (which = 3), y_p = Q x_p (which = 4, the pressure mass
  * matrix), all in natural numbering, FP64, one vector.

@@ -283,9 +283,16 @@ class Problem:
         nh2 = lib().or_hist(self._h, 1, None, 0)
         hist2 = np.zeros(max(nh2, 1))
         lib().or_hist(self._h, 1, _p(hist2), nh2)
+        lanczos = []
+        for which in (2, 3):
+            m = lib().or_hist(self._h, which, None, 0)
+            arr = np.zeros(max(m, 1))
+            lib().or_hist(self._h, which, _p(arr), m)
+            lanczos.append(arr[:m].copy())
         return x, dict(outer=int(info[0]), relres_est=float(info[1]), relres_true=float(info[2]),
                        status=int(info[3]), counts=counts[:n].copy(), qcounts=qcounts[:nq].copy(),
-                       hist=hist[:nh].copy(), hist_res=hist2[:nh2].copy())
+                       hist=hist[:nh].copy(), hist_res=hist2[:nh2].copy(), delta=lanczos[0],
+                       gamma=lanczos[1])
 
     def pcg(self, b, inner_tol, max_inner=1000):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -19,7 +19,7 @@ struct Handle {
   std::vector<int32_t> level, rlevel;
   bool factored = false;
   std::vector<int32_t> counts;
-  std::vector<double> hist, hist2;
+  std::vector<double> hist, hist2, delta, gamma;
   // pressure mass matrix: ordering, IC(0) factor and its levels
   std::vector<int32_t> permQ;
   Csr LQ;
@@ -215,7 +215,7 @@ int or_minres(void* hv, const double* b, double* x, double tol, double inner_tol
          M.forced_q = forced_q; M.nforced_q = forced_q ? nforced_q : 0;
          MinresInfo mi; minres(h->P, M, b, x, tol, max_outer, mi, stop_rule);
          pressure_filter(h->P, x + h->P.n_u); h->counts = M.counts; h->qcounts = M.qcounts;
-         h->hist = mi.hist; h->hist2 = mi.hist2; info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
+         h->hist = mi.hist; h->hist2 = mi.hist2; h->delta = mi.delta; h->gamma = mi.gamma; info[0] = mi.outer; info[1] = mi.relres_est; info[2] = mi.relres_true;
          info[3] = mi.status; return 0;)
 }
 
@@ -233,10 +233,11 @@ int64_t or_counts(void* hv, int32_t* out, int64_t cap) {
   return n;
 }
 
-// which 0: |eta|/gamma_1 after each step; 1: ||b - K x_j|| / ||b|| (STOP_RESIDUAL)
+// which 0: |eta|/gamma_1 after each step; 1: ||b - K x_j|| / ||b|| (STOP_RESIDUAL);
+// 2: Lanczos diagonal delta_j; 3: Lanczos gamma_1, gamma_2, ...
 int64_t or_hist(void* hv, int which, double* out, int64_t cap) {
   Handle* h = static_cast<Handle*>(hv);
-  const std::vector<double>& v = which ? h->hist2 : h->hist;
+  const std::vector<double>& v = which == 0 ? h->hist : which == 1 ? h->hist2 : which == 2 ? h->delta : h->gamma;
   int64_t n = (int64_t)v.size();
   for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
   return n;

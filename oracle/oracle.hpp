@@ -151,6 +151,9 @@ struct MinresInfo {
   int status = 0;  // 0 converged, 1 hit max_outer, 2 breakdown
   std::vector<double> hist;   // |eta|/gamma_1 after each step
   std::vector<double> hist2;  // ||b - K x_j|| / ||b|| after each step (STOP_RESIDUAL)
+  // Lanczos tridiagonal T_j of M^{-1} K in the M-inner product: diagonal
+  // delta_1..delta_j and off-diagonal gamma_2..gamma_{j+1} (gamma[0] = gamma_1)
+  std::vector<double> delta, gamma;
 };
 void spmv(const Csr& M, const double* x, double* y);
 void stokes_apply(const Problem& P, const double* x, double* y);

@@ -245,6 +245,7 @@ void minres(const Problem& P, Precond& M, const double* b, double* x, double tol
   }
   double gamma_prev = 1.0;
   const double gamma1 = gamma;
+  info.gamma.push_back(gamma1);
   double eta = gamma;
   double s_prev = 0.0, s = 0.0, c_prev = 1.0, c = 1.0;
   info.status = 1;
@@ -262,6 +263,8 @@ void minres(const Problem& P, Precond& M, const double* b, double* x, double tol
       break;
     }
     const double gamma_next = std::sqrt(gg);
+    info.delta.push_back(delta);
+    info.gamma.push_back(gamma_next);
     const double a0 = c * delta - c_prev * s * gamma;
     const double a1 = std::sqrt(a0 * a0 + gamma_next * gamma_next);
     const double a2 = s * delta + c_prev * c * gamma;

@@ -59,7 +59,8 @@ class gb_info(C.Structure):
 EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "gb_load_manufactured",
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
             "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel",
-            "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc", "gb_load_cavity"]
+            "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc", "gb_load_cavity",
+            "gb_lanczos", "gb_ritz_extremes"]
 
 
 def library_path() -> str:
@@ -87,6 +88,8 @@ def load_library(build_if_missing: bool = True):
         L.gb_load_fourier.argtypes = [vp, i32, vp, vp, vp]
         L.gb_load_manufactured.argtypes = [vp, vp]
         L.gb_load_cavity.argtypes = [vp, vp]
+        L.gb_lanczos.argtypes = [vp, i32, vp, vp, i32, C.POINTER(i32)]
+        L.gb_ritz_extremes.argtypes = [vp, i32, i32, vp]
         L.gb_factor_ic0.argtypes = [vp, C.POINTER(i64)]
         L.gb_solve.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_solve_host.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
@@ -284,6 +287,25 @@ class Stokes:
         names = {v: k for k, v in self.LAYOUTS.items()}
         names[-1] = "unset"
         return names[a.value], names[b.value]
+
+    def lanczos(self, rhs=0):
+        """Lanczos tridiagonal T_j of the last solve's MINRES for column rhs:
+        (delta_1..delta_j, gamma_1..gamma_{j+1})."""
+        L = load_library()
+        n = C.c_int(0)
+        _check(L.gb_lanczos(self._h, rhs, None, None, 0, C.byref(n)))
+        d = np.zeros(max(n.value, 1))
+        g = np.zeros(n.value + 1)
+        _check(L.gb_lanczos(self._h, rhs, d.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p),
+                            n.value, C.byref(n)))
+        return d[: n.value], g[: n.value + 1]
+
+    def ritz_extremes(self, rhs=0, exclude_one=False):
+        """(lambda^-_min, lambda^-_max, lambda^+_min, lambda^+_max) of the Ritz
+        values of the last solve's Lanczos tridiagonal (column rhs)."""
+        out = np.zeros(4)
+        _check(load_library().gb_ritz_extremes(self._h, rhs, int(exclude_one), out.ctypes.data_as(C.c_void_p)))
+        return out
 
     KERNELS = {"cg_spmv": 0, "ic0_apply": 1, "stokes_apply": 2, "trsv_fwd": 3}
 

@@ -269,6 +269,22 @@ int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv)
   return GB_OK;
 }
 
+int gb_lanczos(gb_ctx* h, int rhs, double* delta_host, double* gamma_host, int cap, int* count) {
+  if (!h || !count) return GB_ERR_INVALID_ARG;
+  return guarded([&] {
+    StreamOrder order(h->c);
+    *count = lanczos_coeffs(h->c, rhs, delta_host, gamma_host, cap);
+  });
+}
+
+int gb_ritz_extremes(gb_ctx* h, int rhs, int exclude_one, double* out_host) {
+  if (!h || !out_host) return GB_ERR_INVALID_ARG;
+  return guarded([&] {
+    StreamOrder order(h->c);
+    ritz_extremes(h->c, rhs, exclude_one, out_host);
+  });
+}
+
 int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
   if (!h || !ms_host) return GB_ERR_INVALID_ARG;
   return guarded([&] {

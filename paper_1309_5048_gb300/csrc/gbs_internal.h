@@ -114,6 +114,8 @@ struct Workspace {
   double* q = nullptr;
   double* b = nullptr;  // right-hand side, internal layout
   double* R = nullptr;  // residual b - K x_j (2-norm stopping rule)
+  double* lz = nullptr;  // Lanczos tridiagonal record [2][K][lz_cap]
+  int lz_cap = 0;
   double* KW[3] = {nullptr, nullptr, nullptr};  // K w_j, rotating like W
   // inner CG, element type T (double or float) stored as raw bytes
   void* cg_x = nullptr;
@@ -235,6 +237,8 @@ double time_kernel(Ctx& c, int which, int reps);
 void dnu(Ctx& c, const double* lam, const double* x, int k, double* out);
 void dnu_noalloc(Ctx& c, const double* lam, const double* x, int k, double* out);
 void release_workspace(Ctx& c);
+int lanczos_coeffs(Ctx& c, int rhs, double* delta, double* gamma, int cap);
+void ritz_extremes(Ctx& c, int rhs, int exclude_one, double* out);
 
 // Velocity DOF decoding shared by host setup code.
 struct Space {

@@ -173,6 +173,8 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.stop_rule = GB_STOP_RESIDUAL;
   a.A_diag = c.A_diag.p;
   a.R = w.R;
+  a.lz = w.lz;
+  a.lz_cap = w.lz_cap;
   a.KW0 = w.KW[0];
   a.KW1 = w.KW[1];
   a.KW2 = w.KW[2];
@@ -701,7 +703,7 @@ void release_workspace(Ctx& c) {
   void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
                   w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
                   w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out, w.qcg_x, w.qcg_r, w.qcg_z,
-                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2]};
+                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2], w.lz};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w.S_host) cudaFreeHost(w.S_host);
@@ -736,6 +738,16 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
   const int K = (k == 1) ? 1 : (k <= 8 ? 8 : 32);
   ensure_workspace(c, K, o.precision, k);
   Workspace& w = c.ws;
+  {
+    // Lanczos record: max_outer steps (and gamma_{max_outer+1}), capped
+    const int cap = std::min(o.max_outer, 1 << 20) + 1;
+    if (!w.lz || w.lz_cap < cap) {
+      if (w.lz) cudaFree(w.lz);
+      w.lz = (double*)dmalloc(sizeof(double) * 2 * (size_t)K * cap);
+      w.lz_cap = cap;
+      w.graph_valid = false;
+    }
+  }
   if (o.forced_q_host) {
     if ((size_t)o.nforced_q > w.forced_q_cap) {
       if (w.forced_q) cudaFree(w.forced_q);
@@ -791,6 +803,88 @@ int solve_host(Ctx& c, const double* rhs_host, double* x_host, int k, const gb_s
   GBS_CUDA(cudaMemcpyAsync(x_host, c.ws.host_out, bytes, cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));
   return st;
+}
+
+// ---- Ritz values (spectral diagnostics) --------------------------------------
+// MINRES is the Lanczos process on M^{-1} K in the M-inner product (Sec. 5):
+// after j steps the tridiagonal T_j (diagonal delta_1..delta_j, off-diagonal
+// gamma_2..gamma_j) represents M^{-1} K on the Krylov space, and its
+// eigenvalues (Ritz values) approximate the eigenvalues of M^{-1} K, the
+// extremal ones first.  The record is written by k_gamma.
+int lanczos_coeffs(Ctx& c, int rhs, double* delta, double* gamma, int cap) {
+  Workspace& w = c.ws;
+  if (!w.lz || w.last_k < 1) fail(GB_ERR_INVALID_ARG, "no completed solve");
+  if (rhs < 0 || rhs >= w.last_k) fail(GB_ERR_INVALID_ARG, "rhs out of range");
+  const int j = std::min((int)w.S_host[S_OUTER_ITS * w.K + rhs], w.lz_cap - 1);
+  const int n = std::min(j, std::max(cap, 0));
+  if (delta && n > 0)
+    GBS_CUDA(cudaMemcpyAsync(delta, w.lz + (size_t)rhs * w.lz_cap, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                             c.stream));
+  if (gamma && cap > 0)
+    GBS_CUDA(cudaMemcpyAsync(gamma, w.lz + (size_t)(w.K + rhs) * w.lz_cap, sizeof(double) * std::min(j + 1, cap + 1),
+                             cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaStreamSynchronize(c.stream));
+  return j;
+}
+
+namespace {
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm
+// sequence of the LDL^T pivots of T - x I).
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+    q = d[i] - x - (i ? off / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// The i-th smallest eigenvalue (0-based) by bisection inside [lo, hi].
+double kth_eigenvalue(const std::vector<double>& d, const std::vector<double>& e, int i, double lo, double hi) {
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(d, e, mid) > i) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+}  // namespace
+
+void ritz_extremes(Ctx& c, int rhs, int exclude_one, double* out) {
+  std::vector<double> d(c.ws.lz_cap > 0 ? c.ws.lz_cap : 1), g(d.size() + 1);
+  const int j = lanczos_coeffs(c, rhs, d.data(), g.data(), (int)d.size());
+  const double nan = std::nan("");
+  for (int i = 0; i < 4; ++i) out[i] = nan;
+  if (j < 1) return;
+  d.resize(j);
+  std::vector<double> e(g.begin() + 1, g.begin() + j);  // gamma_2 .. gamma_j
+  double lo = d[0], hi = d[0];
+  for (int i = 0; i < j; ++i) {  // Gershgorin bounds
+    const double r = (i ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < j ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  lo -= 1e-12 * (std::fabs(lo) + 1.0);
+  hi += 1e-12 * (std::fabs(hi) + 1.0);
+  const int neg = sturm_count(d, e, 0.0);
+  if (neg > 0) {
+    out[0] = kth_eigenvalue(d, e, 0, lo, 0.0);
+    out[1] = kth_eigenvalue(d, e, neg - 1, lo, 0.0);
+  }
+  // positive side, optionally without the Ritz values within 1e-6 of 1
+  int first = neg, last = j - 1;
+  if (exclude_one) {
+    const int c1 = sturm_count(d, e, 1.0 - 1e-6), c2 = sturm_count(d, e, 1.0 + 1e-6);
+    if (first >= c1 && first < c2) first = c2;
+    if (last >= c1 && last < c2) last = c1 - 1;
+  }
+  if (first <= last && first < j) {
+    out[2] = kth_eigenvalue(d, e, first, 0.0, hi);
+    out[3] = kth_eigenvalue(d, e, last, 0.0, hi);
+  }
 }
 
 void apply_operator(Ctx& c, int which, const double* x, double* y) {

@@ -88,6 +88,10 @@ struct Args {
   // K w_j (three rotating buffers, like w) of its recurrence
   int stop_rule;
   double *R, *KW0, *KW1, *KW2;
+  // Lanczos tridiagonal record, per RHS t: delta_j at lz[t * lz_cap + j - 1],
+  // gamma_j at lz[(K + t) * lz_cap + j - 1]
+  double* lz;
+  int lz_cap;
 };
 
 // The two inner CG solves: SYS 0 on A_h (velocity block, Sec. 5.1 "PCG(A)"),
@@ -432,6 +436,7 @@ __global__ void k_gamma(Args a) {
           SF(a, S_GAMMA1, s, K) = gnext;
           SF(a, S_ETA, s, K) = gnext;
           SF(a, S_XCOEF, s, K) = 0.0;
+          if (a.lz && a.lz_cap > 0) a.lz[(size_t)(K + s) * a.lz_cap] = gnext;  // gamma_1
           if (stop || gnext == 0.0) {
             SF(a, S_OUTER_ACTIVE, s, K) = 0.0;
           }
@@ -441,6 +446,10 @@ __global__ void k_gamma(Args a) {
           const double c = SF(a, S_C, s, K), cp = SF(a, S_C_PREV, s, K);
           const double sn = SF(a, S_S, s, K), sp = SF(a, S_S_PREV, s, K);
           (void)gp;
+          if (a.lz && j < a.lz_cap) {  // T_j: delta_j, gamma_{j+1}
+            a.lz[(size_t)s * a.lz_cap + j - 1] = dl;
+            a.lz[(size_t)(K + s) * a.lz_cap + j] = gnext;
+          }
           const double a0 = c * dl - cp * sn * gm;
           const double a1 = sqrt(a0 * a0 + gnext * gnext);
           const double a2 = sn * dl + cp * c * gm;
