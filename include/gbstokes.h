@@ -263,7 +263,10 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * (GB_PREC_*).  spmv: 0 CSR with 8 lanes per row, 1 SELL-32 with one thread
  * per row.  trsv (the IC(0) sweeps): 0 CSR, 1 SELL-32, 2 / 3 / 4 staged (each
  * block stages its rows of a level in shared memory and gathers the solution
- * entries they need in one round trip; about 4 / 12 / 32 entries per lane).
+ * entries they need in one round trip; about 4 / 12 / 32 entries per lane),
+ * 5 / 6 packed (the staged scheme on a k-major copy of each block, so that a
+ * warp gathers the same stencil entry of neighbouring rows; about 12 / 32
+ * entries per lane).
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside

@@ -271,7 +271,8 @@ class Stokes:
         _check(load_library().gb_dnu(self._h, _ptr(lam), _ptr(x), k, out.ctypes.data_as(C.c_void_p)))
         return out
 
-    LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4}
+    LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4, "packed12": 5,
+               "packed32": 6}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
         """Layout of the single-RHS inner SpMV ('csr': 8 lanes per row,

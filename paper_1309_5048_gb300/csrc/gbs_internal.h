@@ -100,6 +100,24 @@ struct Staged {
   int ecap = 0, rcap = 0;                  // over all levels
 };
 
+// Packed copy of the levels of one triangular sweep for the packed
+// single-RHS kernels: the same kind of block partition as Staged (at most
+// kStagedRows rows and kPackedSlots padded slots per block), but each block's
+// entries are stored k-major -- slot k * rows + i holds the k-th entry of the
+// block's row i (column -1 and value 0 past the row's end) -- so that a warp
+// reading consecutive slots reads the same stencil entry of consecutive rows.
+// desc[4b .. 4b+3] = {first row, rows, first slot, slots per row}; level l owns
+// blocks lev_b[l] .. lev_b[l] + lev_nb[l] - 1.  data.src maps slots to CSR
+// positions (-1 for padding) to refill values after factorisation.
+constexpr int kPackedSlots = 2048;
+struct Packed {
+  Sell data;  // col, src, val, val32, slots (off / row0 / rowlen unused)
+  DevBuf<int32_t> desc;
+  std::vector<int32_t> lev_b, lev_nb;
+  std::vector<float> lev_mean;  // mean entries per row of the level
+  int cap = 0, rcap = 0;        // largest block (slots, rows)
+};
+
 struct Workspace {
   int K = 0;          // padded batch width
   int k = 0;          // capacity (right-hand sides) of the staging buffers
@@ -204,11 +222,13 @@ struct Ctx {
   Sell sA, sL, sU;                 // SELL-32 copies of A, L, U
   std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
   Staged tL, tU;                   // staged-sweep partitions of L and U = L^T
+  Packed pL, pU;                   // packed (k-major) copies of L and U
   int n_sm = 0;                    // streaming multiprocessors of the device
   // kernel layout per precision (index 0 FP64, 1 mixed) for single-RHS
   // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row;
   // triangular sweeps 0 CSR, 1 SELL-32, 2/3/4 staged with about 4/12/32
-  // entries per lane; -1 not chosen yet (timed at the first single-RHS solve)
+  // entries per lane, 5/6 packed with about 12/32 entries per lane; -1 not
+  // chosen yet (timed at the first single-RHS solve)
   int var_spmv[2] = {-1, -1}, var_trsv[2] = {-1, -1};
   DevBuf<int> status_d;  // device error flags
   double nu = 1.0, cpen = 0.0;

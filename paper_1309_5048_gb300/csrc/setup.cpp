@@ -364,6 +364,72 @@ void build_staged(const std::vector<int32_t>& ptr, const std::vector<int32_t>& l
   T.desc.upload(desc.data(), desc.size(), stream);
 }
 
+// Packed k-major copy of each level of a sweep over the CSR pattern (ptr,
+// col) for the packed kernels (Packed in gbs_internal.h).  Blocks are cut as
+// in build_staged, with the padded size rows * (longest row) as the cap.
+void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
+                  const std::vector<int32_t>& lev_ptr, int n_sm, Packed& T, cudaStream_t stream) {
+  const int nlev = (int)lev_ptr.size() - 1;
+  std::vector<int32_t> desc, pcol, psrc;
+  T.lev_b.assign(nlev, 0);
+  T.lev_nb.assign(nlev, 0);
+  T.lev_mean.assign(nlev, 0.f);
+  T.cap = T.rcap = 0;
+  auto emit = [&](int32_t rb, int32_t nr, int32_t len) {
+    const int64_t off = (int64_t)pcol.size();
+    if (off + (int64_t)nr * len >= INT32_MAX) fail(GB_ERR_INVALID_ARG, "packed copy exceeds 32-bit indexing");
+    desc.push_back(rb);
+    desc.push_back(nr);
+    desc.push_back((int32_t)off);
+    desc.push_back(len);
+    pcol.resize(off + (int64_t)nr * len, -1);
+    psrc.resize(off + (int64_t)nr * len, -1);
+    for (int32_t i = 0; i < nr; ++i)
+      for (int32_t k = 0; k < ptr[rb + i + 1] - ptr[rb + i]; ++k) {
+        pcol[off + (int64_t)k * nr + i] = col[ptr[rb + i] + k];
+        psrc[off + (int64_t)k * nr + i] = ptr[rb + i] + k;
+      }
+    T.cap = std::max(T.cap, nr * len);
+    T.rcap = std::max(T.rcap, nr);
+  };
+  for (int l = 0; l < nlev; ++l) {
+    const int32_t r0 = lev_ptr[l], r1 = lev_ptr[l + 1];
+    const int64_t R = r1 - r0, E = (int64_t)ptr[r1] - ptr[r0];
+    int64_t nb = std::max<int64_t>((E + kPackedSlots - 1) / kPackedSlots, (R + kStagedRows - 1) / kStagedRows);
+    nb = nb <= n_sm ? std::min<int64_t>(R, n_sm) : (nb + n_sm - 1) / n_sm * n_sm;
+    const double share = (double)(E + 4 * R) / (double)std::max<int64_t>(1, nb);
+    T.lev_b[l] = (int32_t)(desc.size() / 4);
+    T.lev_mean[l] = R ? (float)((double)E / (double)R) : 0.f;
+    int32_t rb = r0, rows = 0, len = 0, cuts = 0;
+    int64_t acc = 0;
+    for (int32_t r = r0; r < r1; ++r) {
+      const int32_t lr = ptr[r + 1] - ptr[r];
+      if (lr > kPackedSlots) fail(GB_ERR_INVALID_ARG, "row too long for the packed sweep");
+      const bool full = (int64_t)(rows + 1) * std::max(len, lr) > kPackedSlots || rows == kStagedRows;
+      const bool due = rows > 0 && (double)(acc + lr + 4) > share * (double)(cuts + 1);
+      if (rows > 0 && (full || due)) {
+        emit(rb, rows, len);
+        ++cuts;
+        rb = r;
+        rows = 0;
+        len = 0;
+      }
+      acc += lr + 4;
+      len = std::max(len, lr);
+      ++rows;
+    }
+    emit(rb, rows, len);
+    T.lev_nb[l] = cuts + 1;
+  }
+  T.desc.upload(desc.data(), desc.size(), stream);
+  Sell& S = T.data;
+  S.slots = (int64_t)pcol.size();
+  S.col.upload(pcol.data(), std::max<size_t>(1, pcol.size()), stream);
+  S.src.upload(psrc.data(), std::max<size_t>(1, psrc.size()), stream);
+  S.val.alloc(std::max<int64_t>(1, S.slots));
+  S.val32.alloc(std::max<int64_t>(1, S.slots));
+}
+
 }  // namespace
 
 void setup_pattern(Ctx& c, const gb_problem& prob) {
@@ -608,6 +674,8 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   }
   build_staged(Lptr, c.lev_ptr, c.n_sm, c.tL, s);
   build_staged(Uptr, c.lev_ptr, c.n_sm, c.tU, s);
+  build_packed(Lptr, Lcol, c.lev_ptr, c.n_sm, c.pL, s);
+  build_packed(Uptr, Ucol, c.lev_ptr, c.n_sm, c.pU, s);
   c.status_d.alloc(16);
   c.status_d.zero(s);
   GBS_CUDA(cudaStreamSynchronize(s));

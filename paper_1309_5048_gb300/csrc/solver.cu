@@ -208,6 +208,34 @@ void staged_allow_smem_one(size_t bytes) {
                                 (int)cudaSharedmemCarveoutMaxShared));
 }
 
+template <class T, bool FWD, int G>
+void packed_allow_smem_one(size_t bytes) {
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_packed<T, FWD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes));
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_packed<T, FWD, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+}
+
+template <class T, bool FWD>
+void packed_allow_smem(size_t bytes) {
+  packed_allow_smem_one<T, FWD, 1>(bytes);
+  packed_allow_smem_one<T, FWD, 2>(bytes);
+  packed_allow_smem_one<T, FWD, 4>(bytes);
+  packed_allow_smem_one<T, FWD, 8>(bytes);
+  packed_allow_smem_one<T, FWD, 16>(bytes);
+  packed_allow_smem_one<T, FWD, 32>(bytes);
+}
+
+// Dynamic shared memory of k_trsv_level_packed (one size for every launch).
+size_t packed_smem_bytes(int cap, int rcap, size_t tsize) {
+  return (size_t)(2 * cap + 2 * rcap) * tsize + (size_t)cap * 4;
+}
+
+template <class T>
+size_t packed_bytes(const Ctx& c) {
+  return packed_smem_bytes(std::max(c.pL.cap, c.pU.cap), std::max(c.pL.rcap, c.pU.rcap), sizeof(T));
+}
+
 template <class T, bool FWD>
 void staged_allow_smem(size_t bytes) {
   staged_allow_smem_one<T, FWD, 1>(bytes);
@@ -233,6 +261,19 @@ template <class T>
 void staged_prepare(Ctx& c) {
   staged_allow_smem<T, true>(staged_bytes<T>(c));
   staged_allow_smem<T, false>(staged_bytes<T>(c));
+  packed_allow_smem<T, true>(packed_bytes<T>(c));
+  packed_allow_smem<T, false>(packed_bytes<T>(c));
+}
+
+template <class T>
+const T* pick_host(const double* d, const float* f);
+template <>
+const double* pick_host<double>(const double* d, const float*) {
+  return d;
+}
+template <>
+const float* pick_host<float>(const double*, const float* f) {
+  return f;
 }
 
 int grid_cap(int64_t threads) {
@@ -266,8 +307,39 @@ struct Run {
     GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_staged<T, FWD, GG>, a, (const int4*)st.desc.p + st.lev_b[l],
                                 std::max(c.tL.ecap, c.tU.ecap), std::max(c.tL.rcap, c.tU.rcap)));
   }
+  template <bool FWD, int GG>
+  void packed_level(cudaLaunchConfig_t& cfg, const Packed& pk, int l) {
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_packed<T, FWD, GG>, a, (const int4*)pk.desc.p + pk.lev_b[l],
+                                (const int32_t*)pk.data.col.p, pick_host<T>(pk.data.val.p, pk.data.val32.p),
+                                std::max(c.pL.cap, c.pU.cap), std::max(c.pL.rcap, c.pU.rcap)));
+  }
   template <bool FWD>
   void level(int l) {
+    if (K == 1 && vtrsv >= 5) {
+      const Packed& pk = FWD ? c.pL : c.pU;
+      const float per_lane = vtrsv == 5 ? 12.f : 32.f;
+      int lanes = 1;
+      while (lanes < 32 && pk.lev_mean[l] > per_lane * (float)lanes) lanes *= 2;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)pk.lev_nb[l]);
+      cfg.blockDim = dim3(kBlock);
+      cfg.dynamicSmemBytes = packed_bytes<T>(c);
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      switch (lanes) {
+        case 1: packed_level<FWD, 1>(cfg, pk, l); break;
+        case 2: packed_level<FWD, 2>(cfg, pk, l); break;
+        case 4: packed_level<FWD, 4>(cfg, pk, l); break;
+        case 8: packed_level<FWD, 8>(cfg, pk, l); break;
+        case 16: packed_level<FWD, 16>(cfg, pk, l); break;
+        default: packed_level<FWD, 32>(cfg, pk, l); break;
+      }
+      return;
+    }
     if (K == 1 && vtrsv >= 2) {
       const Staged& st = FWD ? c.tL : c.tU;
       const float per_lane = vtrsv == 2 ? 4.f : (vtrsv == 3 ? 12.f : 32.f);
@@ -517,9 +589,10 @@ struct Run {
 };
 
 // Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
-// SELL-32 (thread per row) forms of the inner SpMV, and the CSR, SELL-32 and
-// three staged forms (about 4, 12, 32 entries per lane) of one IC(0)
-// application, on this problem, and keep the fastest; a form replaces the
+// SELL-32 (thread per row) forms of the inner SpMV, and the CSR, SELL-32,
+// three staged (about 4, 12, 32 entries per lane) and two packed (about 12,
+// 32 entries per lane) forms of one IC(0) application, on this problem, and
+// keep the fastest; a form replaces the
 // best so far only when it is 3% faster.  Runs once per precision, outside
 // any graph capture; the choice only changes the summation order inside a row.
 template <class T>
@@ -562,7 +635,7 @@ void autotune_single(Ctx& c) {
   if (c.var_trsv[pi] < 0) {
     float best = time_it(0, 1);
     int choice = 0;
-    for (int v = 1; v <= 4; ++v) {
+    for (int v = 1; v <= 6; ++v) {
       const float t = time_it(v, 1);
       if (t < 0.97f * best) {
         best = t;

@@ -921,6 +921,96 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_staged(Args a, const int4
   }
 }
 
+// ---- packed variant (single right-hand side) ------------------------------
+// One level of a triangular solve (same recurrences as k_trsv_level) over the
+// packed k-major copy of the level (build_packed): block b owns rows
+// [desc.x, desc.x + desc.y) and slots [desc.z, desc.z + desc.y * desc.w),
+// slot k * rows + i holding the k-th entry of row i (column -1, value 0 past
+// its end).  The slots are staged in shared memory before the wait for the
+// previous level; after it, consecutive threads gather the solution entries
+// of consecutive slots -- the same stencil entry of neighbouring rows, so a
+// warp touches few memory sectors -- and G lanes per row sum value * entry
+// over k (padding contributes exact zeros).  Shared memory: T val[cap],
+// T xg[cap], T rhs[rcap], T inv[rcap], int col[cap].
+template <class T, bool FWD, int G>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_packed(Args a, const int4* __restrict__ desc,
+                                                              const int32_t* __restrict__ pcol,
+                                                              const T* __restrict__ pval, int cap, int rcap) {
+  constexpr int EPT = kPackedSlots / kBlock;  // slots per thread
+  static_assert(EPT * kBlock == kPackedSlots && kStagedRows <= kBlock, "packed block shape");
+  extern __shared__ __align__(16) unsigned char packed_smem[];
+  cudaTriggerProgrammaticLaunchCompletion();
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  T* sv = (T*)packed_smem;
+  T* sx = sv + cap;
+  T* sr = sx + cap;
+  T* si = sr + rcap;
+  int* sc = (int*)(si + rcap);
+  const int tid = threadIdx.x;
+  const int4 d = desc[blockIdx.x];
+  const int rb = d.x, nr = d.y, off = d.z, len = d.w;
+  const int ns = nr * len;
+  {
+    int cv[EPT];
+    T vv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      cv[u] = q < ns ? pcol[off + q] : -1;
+      vv[u] = q < ns ? pval[off + q] : T(0);
+    }
+    const T iv = tid < nr ? inv[rb + tid] : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      if (q < ns) {
+        sc[q] = cv[u];
+        sv[q] = vv[u];
+      }
+    }
+    if (tid < nr) si[tid] = iv;
+  }
+  cudaGridDependencySynchronize();
+  __syncthreads();
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // read with the gathers; decides the stores
+  {
+    T xv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      const int cc = q < ns ? sc[q] : -1;
+      xv[u] = cc >= 0 ? __ldcg(out + cc) : T(0);
+    }
+    const T rv = tid < nr ? __ldcg(rhs + rb + tid) : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      if (q < ns) sx[q] = xv[u];
+    }
+    if (tid < nr) sr[tid] = rv;
+  }
+  __syncthreads();
+  if (!live) return;
+  const int g = tid % G;
+  for (int i = tid / G; i < nr; i += kBlock / G) {  // uniform over a lane group
+    T s0 = 0, s1 = 0;
+    int k = g;
+    for (; k + G < len; k += 2 * G) {
+      s0 += sv[k * nr + i] * sx[k * nr + i];
+      s1 += sv[(k + G) * nr + i] * sx[(k + G) * nr + i];
+    }
+    if (k < len) s0 += sv[k * nr + i] * sx[k * nr + i];
+    T s = s0 + s1;
+    if (G > 1) {
+      if (sizeof(T) == 8) s = (T)group_sum<G>((double)s);
+      else s = (T)group_sumf<G>((float)s);
+    }
+    if (g == 0) out[rb + i] = (sr[i] - s) * si[i];
+  }
+}
+
 // x[i] = v (kernel timing and layout tuning only).
 template <class T>
 __global__ void k_fill_value(T* __restrict__ x, int64_t n, T v) {

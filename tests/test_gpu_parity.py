@@ -290,16 +290,16 @@ def test_edge_cases(oracle_mod, gb):
 
 
 LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr"), ("csr", "staged4"),
-                ("sell", "staged12"), ("csr", "staged32")]
+                ("sell", "staged12"), ("csr", "staged32"), ("csr", "packed12"), ("sell", "packed32")]
 
 
 @pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
 @pytest.mark.parametrize("dim,N,p", [(2, 13, 3), (3, 3, 3), (2, 40, 4)])
 def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p):
     """Every single-RHS layout of the inner SpMV (CSR 8 lanes per row,
-    SELL-32 thread per row) and of the IC(0) sweeps (also the staged forms,
-    whose levels are split over many blocks at 2D 40^2) reproduces the
-    oracle (<= 1e-10)."""
+    SELL-32 thread per row) and of the IC(0) sweeps (also the staged and
+    packed forms, whose levels are split over many blocks at 2D 40^2)
+    reproduces the oracle (<= 1e-10)."""
     ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
     assert ref.factor() < 0
     s.factor_ic0()
@@ -322,7 +322,8 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     _, rhs = _rhs(oracle_mod.Problem(2, 20, 3), s, "fourier", seed=3)
     s.solve(rhs, tol=1e-6)
     spmv, trsv = s.kernel_variants("fp64")
-    assert spmv in ("csr", "sell") and trsv in ("csr", "sell", "staged4", "staged12", "staged32")
+    assert spmv in ("csr", "sell") and trsv in ("csr", "sell", "staged4", "staged12", "staged32", "packed12",
+                                                 "packed32")
 
 
 @pytest.mark.slow
