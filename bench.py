@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d256")
     ap.add_argument("--ordering", choices=["natural", "rcm", "multicolour"], default="multicolour")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--spmv", choices=["auto", "csr", "sell"], default="auto",
+    ap.add_argument("--spmv", choices=["auto", "csr", "sell", "sell2w", "sell4w"], default="auto",
                     help="single-RHS SpMV layout of the benchmark precision (auto: timed at the first solve)")
     ap.add_argument("--trsv", choices=["auto", "csr", "sell", "staged4", "staged12", "staged32", "packed12",
                                        "packed32"], default="auto",

@@ -261,7 +261,7 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
 /* Kernel layout of single-right-hand-side solves (k == 1) for one precision
  * (GB_PREC_*).  spmv: 0 CSR with 8 lanes per row, 1 SELL-32 with one thread
- * per row.  trsv (the IC(0) sweeps): 0 CSR, 1 SELL-32, 2 / 3 / 4 staged (each
+ * per row, 2 / 3 SELL-32 with 2 / 4 warps per 32-row slice.  trsv (the IC(0) sweeps): 0 CSR, 1 SELL-32, 2 / 3 / 4 staged (each
  * block stages its rows of a level in shared memory and gathers the solution
  * entries they need in one round trip; about 4 / 12 / 32 entries per lane),
  * 5 / 6 packed (the staged scheme on a k-major copy of each block, so that a

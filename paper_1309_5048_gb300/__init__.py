@@ -273,21 +273,24 @@ class Stokes:
 
     LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4, "packed12": 5,
                "packed32": 6}
+    SPMV_LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "sell2w": 2, "sell4w": 3}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
         """Layout of the single-RHS inner SpMV ('csr': 8 lanes per row,
-        'sell': SELL-32, one thread per row) and IC(0) sweeps (also 'staged4',
-        'staged12', 'staged32': rows staged in shared memory, about 4/12/32
-        entries per lane), or 'auto'."""
-        _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.LAYOUTS[spmv],
+        'sell': SELL-32, one thread per row, 'sell2w' / 'sell4w': SELL-32 with
+        2 / 4 warps per slice) and IC(0) sweeps ('csr', 'sell', 'staged4',
+        'staged12', 'staged32': rows staged in shared memory, 'packed12',
+        'packed32': k-major copies), or 'auto'."""
+        _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.SPMV_LAYOUTS[spmv],
                                                       self.LAYOUTS[trsv]))
 
     def kernel_variants(self, precision="fp64"):
         a, b = C.c_int(0), C.c_int(0)
         _check(load_library().gb_get_kernel_variants(self._h, PRECISIONS[precision], C.byref(a), C.byref(b)))
         names = {v: k for k, v in self.LAYOUTS.items()}
-        names[-1] = "unset"
-        return names[a.value], names[b.value]
+        snames = {v: k for k, v in self.SPMV_LAYOUTS.items()}
+        names[-1] = snames[-1] = "unset"
+        return snames[a.value], names[b.value]
 
     def lanczos(self, rhs=0):
         """Lanczos tridiagonal T_j of the last solve's MINRES for column rhs:

@@ -225,7 +225,8 @@ struct Ctx {
   Packed pL, pU;                   // packed (k-major) copies of L and U
   int n_sm = 0;                    // streaming multiprocessors of the device
   // kernel layout per precision (index 0 FP64, 1 mixed) for single-RHS
-  // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row;
+  // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row,
+  // 2/3 SELL-32 with 2/4 warps per slice;
   // triangular sweeps 0 CSR, 1 SELL-32, 2/3/4 staged with about 4/12/32
   // entries per lane, 5/6 packed with about 12/32 entries per lane; -1 not
   // chosen yet (timed at the first single-RHS solve)

@@ -383,7 +383,9 @@ struct Run {
     else GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
   }
   void spmv() {
-    if (K == 1 && vspmv == 1) k_cg_spmv_sell<T><<<grid_cap((int64_t)c.sA.nslices * 32), kBlock, 0, s>>>(a);
+    if (K == 1 && vspmv == 2) k_cg_spmv_sellw<T, 2><<<grid_cap((int64_t)c.sA.nslices * 64), kBlock, 0, s>>>(a);
+    else if (K == 1 && vspmv == 3) k_cg_spmv_sellw<T, 4><<<grid_cap((int64_t)c.sA.nslices * 128), kBlock, 0, s>>>(a);
+    else if (K == 1 && vspmv == 1) k_cg_spmv_sell<T><<<grid_cap((int64_t)c.sA.nslices * 32), kBlock, 0, s>>>(a);
     else k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
   }
   void trsv_fwd() {
@@ -589,7 +591,8 @@ struct Run {
 };
 
 // Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
-// SELL-32 (thread per row) forms of the inner SpMV, and the CSR, SELL-32,
+// SELL-32 (thread per row; 2 or 4 warps per slice) forms of the inner SpMV,
+// and the CSR, SELL-32,
 // three staged (about 4, 12, 32 entries per lane) and two packed (about 12,
 // 32 entries per lane) forms of one IC(0) application, on this problem, and
 // keep the fastest; a form replaces the
@@ -631,7 +634,18 @@ void autotune_single(Ctx& c) {
     GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     return ms;
   };
-  if (c.var_spmv[pi] < 0) c.var_spmv[pi] = time_it(1, 0) < 0.97f * time_it(0, 0) ? 1 : 0;
+  if (c.var_spmv[pi] < 0) {
+    float best = time_it(0, 0);
+    int choice = 0;
+    for (int v = 1; v <= 3; ++v) {
+      const float t = time_it(v, 0);
+      if (t < 0.97f * best) {
+        best = t;
+        choice = v;
+      }
+    }
+    c.var_spmv[pi] = choice;
+  }
   if (c.var_trsv[pi] < 0) {
     float best = time_it(0, 1);
     int choice = 0;

@@ -775,6 +775,59 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_sell(Args a) {
   }
 }
 
+// q = A p and p^T q on the SELL-32 copy with W warps per 32-row slice: warp h
+// of a slice sums the slots k = h, h + W, ... of its rows (coalesced loads of
+// the same stencil entry of 32 rows), the W partial sums are added in a fixed
+// order in shared memory.  More warps in flight than one thread per row when
+// rows are long and slices few.  Epilogue as k_cg_spmv.
+template <class T, int W>
+__global__ void __launch_bounds__(kBlock) k_cg_spmv_sellw(Args a) {
+  constexpr int SPB = kBlock / (32 * W);  // slices per block
+  static_assert(SPB * 32 * W == kBlock, "block shape");
+  __shared__ T part[W][SPB][32];
+  const SellView m = a.sA;
+  const T* __restrict__ val = pick<T>(m.val, m.val32);
+  const T* __restrict__ p = (const T*)a.cg_p;
+  T* __restrict__ q = (T*)a.cg_q;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = warp % W, ls = warp / W;
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;
+  double vals[1] = {0.0};
+  for (int s0 = blockIdx.x * SPB; s0 < m.nslices; s0 += gridDim.x * SPB) {  // uniform over the block
+    const int s = s0 + ls;
+    int row = -1;
+    T y = 0;
+    if (live && s < m.nslices) {
+      row = m.row0[s] + lane;
+      if (row < m.row0[s + 1]) {
+        const int base = m.off[s] + lane, len = m.rowlen[row];
+        for (int k = h; k < len; k += W) y += val[base + 32 * k] * p[m.col[base + 32 * k]];
+      } else {
+        row = -1;
+      }
+    }
+    part[h][ls][lane] = y;
+    __syncthreads();
+    if (h == 0 && row >= 0) {
+      T t = part[0][ls][lane];
+#pragma unroll
+      for (int u = 1; u < W; ++u) t += part[u][ls][lane];
+      q[row] = t;
+      vals[0] += (double)t * (double)p[row];
+    }
+    __syncthreads();
+  }
+  block_partials<1, 1>(vals, a.partial);
+  if (last_block(a.counter)) {
+    __shared__ double tot[1];
+    finalize_partials<1, 1>(a.partial, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      if (SF(a, S_CG_ACTIVE, 0, 1) != 0.0) SF(a, S_ALPHA, 0, 1) = SF(a, S_RHO, 0, 1) / tot[0];
+      *a.counter = 0;
+    }
+  }
+}
+
 // One level of a triangular solve over the slices [s0, s1) of that level
 // (same recurrences and the same programmatic-dependent-launch structure as
 // k_trsv_level).
