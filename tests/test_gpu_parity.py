@@ -237,7 +237,7 @@ def test_autograd_function_against_finite_differences(oracle_mod, gb):
     nu = torch.tensor(nu0, dtype=torch.float64, device="cuda", requires_grad=True)
     opts = dict(tol=1e-13, inner_tol=1e-3)
     x = stokes_solve(f, nu, s, **opts)
-    ut = torch.tensor(target_velocity(s.n_u, float(x[: s.n_u].pow(2).mean().sqrt())), device="cuda")
+    ut = torch.tensor(target_velocity(s.n_u, float(x.detach()[: s.n_u].pow(2).mean().sqrt())), device="cuda")
     loss = 0.5 * (x[: s.n_u] - ut).pow(2).sum()
     loss.backward()
 
