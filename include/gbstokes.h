@@ -275,6 +275,16 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
 int gb_set_kernel_variants(gb_ctx* ctx, int precision, int spmv, int trsv);
 int gb_get_kernel_variants(const gb_ctx* ctx, int precision, int* spmv, int* trsv);
 
+/* IC(0) sweep kernel of batched solves (k > 1; width 8 for k <= 8, 32 for
+ * k <= 32) for one precision: 0 one row per lane group with the column
+ * indices read as it goes, 1 staged (each row's indices and values copied to
+ * shared memory before the wait for the previous level, then the solution
+ * entries loaded 16 at a time), -1 automatic (timed at the first batched
+ * solve of that precision and width; the faster by 3 % is kept).  Both sum
+ * in the same order.  gb_get_batch_sweep reports the choice (-1: not made). */
+int gb_set_batch_sweep(gb_ctx* ctx, int precision, int width, int variant);
+int gb_get_batch_sweep(const gb_ctx* ctx, int precision, int width, int* variant);
+
 /* Benchmark instrumentation.  Times `reps` (>= 1) launches of one kernel
  * family of the most recent gb_solve, with the same batch width, precision
  * and launch configuration, on the context's stream with CUDA events, after

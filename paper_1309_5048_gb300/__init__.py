@@ -60,7 +60,7 @@ EXPORTED = ["gb_setup_pattern", "gb_sizes", "gb_assemble", "gb_load_fourier", "g
             "gb_factor_ic0", "gb_solve", "gb_solve_host", "gb_solve_adjoint", "gb_dnu", "gb_apply",
             "gb_export", "gb_destroy", "gb_status_string", "gb_last_error", "gb_time_kernel",
             "gb_set_kernel_variants", "gb_get_kernel_variants", "gb_dnu_noalloc", "gb_load_cavity",
-            "gb_lanczos", "gb_ritz_extremes"]
+            "gb_lanczos", "gb_ritz_extremes", "gb_set_batch_sweep", "gb_get_batch_sweep"]
 
 
 def library_path() -> str:
@@ -90,6 +90,8 @@ def load_library(build_if_missing: bool = True):
         L.gb_load_cavity.argtypes = [vp, vp]
         L.gb_lanczos.argtypes = [vp, i32, vp, vp, i32, C.POINTER(i32)]
         L.gb_ritz_extremes.argtypes = [vp, i32, i32, vp]
+        L.gb_set_batch_sweep.argtypes = [vp, i32, i32, i32]
+        L.gb_get_batch_sweep.argtypes = [vp, i32, i32, C.POINTER(i32)]
         L.gb_factor_ic0.argtypes = [vp, C.POINTER(i64)]
         L.gb_solve.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
         L.gb_solve_host.argtypes = [vp, vp, vp, i32, C.POINTER(gb_solve_opts), vp]
@@ -291,6 +293,18 @@ class Stokes:
         snames = {v: k for k, v in self.SPMV_LAYOUTS.items()}
         names[-1] = snames[-1] = "unset"
         return snames[a.value], names[b.value]
+
+    BATCH_SWEEPS = {"auto": -1, "warp": 0, "staged": 1}
+
+    def set_batch_sweep(self, precision="fp64", width=32, variant="auto"):
+        """IC(0) sweep kernel of batched solves of this width (8 or 32)."""
+        _check(load_library().gb_set_batch_sweep(self._h, PRECISIONS[precision], width,
+                                                  self.BATCH_SWEEPS[variant]))
+
+    def batch_sweep(self, precision="fp64", width=32):
+        v = C.c_int(0)
+        _check(load_library().gb_get_batch_sweep(self._h, PRECISIONS[precision], width, C.byref(v)))
+        return {val: key for key, val in self.BATCH_SWEEPS.items()}[v.value]
 
     def lanczos(self, rhs=0):
         """Lanczos tridiagonal T_j of the last solve's MINRES for column rhs:

@@ -259,6 +259,25 @@ int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
   return GB_OK;
 }
 
+int gb_set_batch_sweep(gb_ctx* h, int precision, int width, int variant) {
+  if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || variant < -1 || variant > 1) {
+    set_error("bad batch sweep request");
+    return GB_ERR_INVALID_ARG;
+  }
+  h->c.var_trsv_batch[precision][width == 8 ? 0 : 1] = variant;
+  h->c.ws.graph_valid = false;
+  return GB_OK;
+}
+
+int gb_get_batch_sweep(const gb_ctx* h, int precision, int width, int* variant) {
+  if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || !variant) {
+    set_error("bad batch sweep query");
+    return GB_ERR_INVALID_ARG;
+  }
+  *variant = h->c.var_trsv_batch[precision][width == 8 ? 0 : 1];
+  return GB_OK;
+}
+
 int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv) {
   if (!h || precision < 0 || precision > 1 || !spmv || !trsv) {
     set_error("bad kernel variant query");

@@ -231,6 +231,10 @@ struct Ctx {
   // entries per lane, 5/6 packed with about 12/32 entries per lane; -1 not
   // chosen yet (timed at the first single-RHS solve)
   int var_spmv[2] = {-1, -1}, var_trsv[2] = {-1, -1};
+  // batched sweeps per precision and width (index 0: K = 8, 1: K = 32): 0 the
+  // warp-per-row kernel, 1 the staged batched kernel, -1 not chosen yet
+  int var_trsv_batch[2][2] = {{-1, -1}, {-1, -1}};
+  int max_lrow = 0;  // longest off-diagonal row of L and U
   DevBuf<int> status_d;  // device error flags
   double nu = 1.0, cpen = 0.0;
   bool assembled = false, factored = false;

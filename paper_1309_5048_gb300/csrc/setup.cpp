@@ -676,6 +676,9 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   build_staged(Uptr, c.lev_ptr, c.n_sm, c.tU, s);
   build_packed(Lptr, Lcol, c.lev_ptr, c.n_sm, c.pL, s);
   build_packed(Uptr, Ucol, c.lev_ptr, c.n_sm, c.pU, s);
+  c.max_lrow = 0;
+  for (int64_t r = 0; r < n; ++r)
+    c.max_lrow = std::max({c.max_lrow, Lptr[r + 1] - Lptr[r], Uptr[r + 1] - Uptr[r]});
   c.status_d.alloc(16);
   c.status_d.zero(s);
   GBS_CUDA(cudaStreamSynchronize(s));

@@ -257,8 +257,23 @@ size_t staged_bytes(const Ctx& c) {
 
 // Raise the dynamic shared-memory limit of the staged sweep kernels to what
 // the partitions of this problem need (outside any graph capture).
+// Shared memory and row capacity of k_trsv_level_batch.
+int batch_capr(const Ctx& c) { return std::max(1, std::min(c.max_lrow, 512)); }
+template <int K, class T>
+size_t batch_bytes(const Ctx& c) {
+  return (size_t)(kBlock / K) * batch_capr(c) * (sizeof(T) + 4);
+}
+template <int K, class T>
+void batch_allow_smem(const Ctx& c) {
+  const int b = (int)batch_bytes<K, T>(c);
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_batch<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_batch<K, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+}
+
 template <class T>
 void staged_prepare(Ctx& c) {
+  batch_allow_smem<8, T>(c);
+  batch_allow_smem<32, T>(c);
   staged_allow_smem<T, true>(staged_bytes<T>(c));
   staged_allow_smem<T, false>(staged_bytes<T>(c));
   packed_allow_smem<T, true>(packed_bytes<T>(c));
@@ -287,11 +302,13 @@ struct Run {
   Args a;
   cudaStream_t s;
   int vspmv = 0, vtrsv = 0;  // single-RHS layouts (Ctx::var_spmv, Ctx::var_trsv)
+  int vbatch = 0;            // batched sweep (Ctx::var_trsv_batch)
   static constexpr int G = Map<K>::G;
   Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {
     const int pi = std::is_same<T, float>::value ? 1 : 0;
     vspmv = K == 1 ? std::max(0, c.var_spmv[pi]) : 0;
     vtrsv = K == 1 ? std::max(0, c.var_trsv[pi]) : 0;
+    vbatch = K == 1 ? 0 : std::max(0, c.var_trsv_batch[pi][K == 8 ? 0 : 1]);
   }
   int64_t n() const { return c.n_u + c.n_p; }
 
@@ -363,6 +380,22 @@ struct Run {
         case 16: staged_level<FWD, 16>(cfg, st, l); break;
         default: staged_level<FWD, 32>(cfg, st, l); break;
       }
+      return;
+    }
+    if (K > 1 && vbatch == 1) {
+      constexpr int KB = K > 1 ? K : 8;  // (K == 1 never reaches here)
+      const int r0 = c.lev_ptr[l], r1 = c.lev_ptr[l + 1];
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((r1 - r0 + kBlock / KB - 1) / (kBlock / KB)));
+      cfg.blockDim = dim3(kBlock);
+      cfg.dynamicSmemBytes = batch_bytes<KB, T>(c);
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_batch<KB, T, FWD>, a, r0, r1, batch_capr(c)));
       return;
     }
     const bool sell = (K == 1 && vtrsv == 1);
@@ -663,9 +696,48 @@ void autotune_single(Ctx& c) {
   GBS_CUDA(cudaGetLastError());
 }
 
+// Batched sweep tuning: time one IC(0) application of the warp-per-row and
+// the staged batched kernels at width K and keep the faster (3 % margin).
+template <int K, class T>
+void autotune_batch(Ctx& c) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0, ki = K == 8 ? 0 : 1;
+  staged_prepare<T>(c);
+  if (c.var_trsv_batch[pi][ki] >= 0) return;
+  Workspace& w = c.ws;
+  k_fill_value<T><<<grid_cap(c.n_u * K), kBlock, 0, c.stream>>>((T*)w.cg_r, c.n_u * K, T(1));
+  std::vector<double> live(K, 1.0);
+  GBS_CUDA(cudaMemcpyAsync(w.S + S_CG_ACTIVE * K, live.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c.stream));
+  Args a = make_args(c, nullptr, K);
+  cudaEvent_t e0, e1;
+  GBS_CUDA(cudaEventCreate(&e0));
+  GBS_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](int variant) {
+    Run<K, T> run(c, a);
+    run.vbatch = variant;
+    run.trsv_fwd();
+    run.trsv_bwd();
+    GBS_CUDA(cudaEventRecord(e0, c.stream));
+    for (int r = 0; r < 3; ++r) {
+      run.trsv_fwd();
+      run.trsv_bwd();
+    }
+    GBS_CUDA(cudaEventRecord(e1, c.stream));
+    GBS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  const float t0 = time_it(0), t1 = time_it(1);
+  c.var_trsv_batch[pi][ki] = t1 < 0.97f * t0 ? 1 : 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GBS_CUDA(cudaGetLastError());
+}
+
 template <int K, class T>
 void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solve_opts& o) {
   if (K == 1) autotune_single<T>(c);
+  if (K > 1) autotune_batch<K, T>(c);
   Args a = make_args(c, &o, k);
   Run<K, T> run(c, a);
   Workspace& w = c.ws;
@@ -677,7 +749,7 @@ void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solv
                              (double)o.max_outer, (double)o.max_inner, (double)K, (double)o.precision,
                              (double)a.nforced, c.nu, (double)run.vspmv, (double)run.vtrsv,
                              (double)o.pressure_block, (double)a.nforced_q, (double)o.stop_rule,
-                             (double)o.velocity_block};
+                             (double)o.velocity_block, (double)run.vbatch};
   if (!w.graph_valid || w.graph_key != key) {
     if (w.graph) {
       cudaGraphExecDestroy(w.graph);

@@ -737,6 +737,65 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level(Args a, int r0, int r1) {
   if (live && (K > 1 || g == 0)) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
 }
 
+// ---- staged batched variant (K = 8 or 32 right-hand sides) ---------------
+// One level for k right-hand sides (same recurrences as k_trsv_level), K lanes
+// per row (lane t = right-hand side t).  Before the wait for the previous
+// level each row's column indices and factor values (up to capr of them) are
+// copied to shared memory, so that after the wait every lane can issue the
+// loads of its solution entries x[col * K + t] -- one coalesced K-wide segment
+// per entry -- 16 at a time without waiting for the indices; entries past
+// capr are read from global memory.  Same summation order as k_trsv_level.
+// Dynamic shared memory: T val[kBlock / K][capr], int col[kBlock / K][capr].
+template <int K, class T, bool FWD>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_batch(Args a, int r0, int r1, int capr) {
+  constexpr int RPB = kBlock / K;  // rows per block
+  constexpr int CH = 16;           // solution loads in flight per lane
+  extern __shared__ __align__(16) unsigned char batch_smem[];
+  cudaTriggerProgrammaticLaunchCompletion();
+  const int32_t* __restrict__ ptr = FWD ? a.L_ptr : a.U_ptr;
+  const int32_t* __restrict__ col = FWD ? a.L_col : a.U_col;
+  const T* __restrict__ val = FWD ? pick<T>(a.L_val, a.L_val32) : pick<T>(a.U_val, a.U_val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  T* sv = (T*)batch_smem;
+  int* sc = (int*)(sv + RPB * capr);
+  const int t = threadIdx.x % K, lr = threadIdx.x / K;
+  const int row = r0 + blockIdx.x * RPB + lr;
+  const bool act = row < r1;  // uniform over a lane group
+  int eb = 0, ee = 0, n = 0;
+  T ii = T(0);
+  T* rv = sv + lr * capr;
+  int* rc = sc + lr * capr;
+  if (act) {
+    eb = ptr[row];
+    ee = ptr[row + 1];
+    n = min(ee - eb, capr);
+    for (int j = t; j < n; j += K) {
+      rc[j] = col[eb + j];
+      rv[j] = val[eb + j];
+    }
+    ii = inv[row];
+  }
+  cudaGridDependencySynchronize();
+  __syncthreads();
+  if (!act) return;  // uniform over a lane group, after the barrier
+  const bool live = SF(a, S_CG_ACTIVE, t, K) != 0.0;  // decides the store only
+  T s = 0;
+  int j = 0;
+  for (; j + CH <= n; j += CH) {
+    T xv[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) xv[u] = __ldcg(out + (size_t)rc[j + u] * K + t);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) s += rv[j + u] * xv[u];
+  }
+  for (; j < n; ++j) s += rv[j] * __ldcg(out + (size_t)rc[j] * K + t);
+  for (int e = eb + n; e < ee; ++e) s += val[e] * __ldcg(out + (size_t)col[e] * K + t);
+  const size_t ridx = (size_t)row * K + t;
+  if (live) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
+}
+
 // ---- SELL-32 variants (single right-hand side, one thread per row) --------
 // The 32 lanes of a warp read 32 consecutive slots, so every load of values
 // and column indices is coalesced and no cross-lane reduction is needed (on

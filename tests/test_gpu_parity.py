@@ -166,6 +166,42 @@ def test_solve_free_mode(oracle_mod, gb, precision, ordering):
     assert rel(x10.cpu().numpy(), xr10) <= 1e-7
 
 
+@pytest.mark.parametrize("variant", ["warp", "staged"])
+def test_batched_sweep_kernels_agree(oracle_mod, gb, variant):
+    """Both batched IC(0) sweep kernels (widths 8 and 32, FP64 and mixed)
+    give each column the oracle's solution (free mode).  FP64 at 1e-12 within
+    1e-9; mixed at 1e-10 within 10x the error of the oracle's own 1e-10 solve
+    against a 1e-13 one (3D: K's condition number turns 1e-10 residuals into
+    ~1e-7 solution differences), and at least 1e-6."""
+    from paper_1309_5048_gb300.inputs import fourier_modes
+    ref, s = make_pair(oracle_mod, gb, 3, 4, 3, "multicolour")
+    assert ref.factor() < 0
+    s.factor_ic0()
+    for prec in ("fp64", "mixed"):
+        for w in (8, 32):
+            s.set_batch_sweep(prec, w, variant)
+    for k in (5, 20):
+        rhs = torch.zeros(k, s.n, dtype=torch.float64, device="cuda")
+        bs = []
+        for t in range(k):
+            kappa, amp = fourier_modes(3, seed=300 + t)
+            rhs[t, : s.n_u] = s.load_fourier(kappa, amp)
+            bs.append(np.concatenate([ref.load_fourier(kappa, amp), np.zeros(ref.n_p)]))
+        for prec, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+            X, infos = s.solve(rhs, tol=tol, inner_tol=1e-2, precision=prec)
+            X = X.cpu().numpy()
+            for t in (0, k - 1):
+                xr, _ = ref.minres(bs[t], tol=tol, inner_tol=1e-2)
+                assert infos[t]["status"] == 0
+                if prec == "fp64":
+                    assert rel(X[t], xr) <= 1e-9, (variant, k, prec, t, rel(X[t], xr))
+                else:
+                    xt, _ = ref.minres(bs[t], tol=1e-13, inner_tol=1e-2)
+                    bound = max(10 * rel(xr, xt), 1e-6)
+                    assert rel(X[t], xt) <= bound, (variant, k, prec, t, rel(X[t], xt), bound)
+    assert s.batch_sweep("fp64", 8) == variant and s.batch_sweep("mixed", 32) == variant
+
+
 def test_batched_columns_match_single_solves(oracle_mod, gb):
     """k right-hand sides in one launch (K = 8 and K = 32 layouts): each
     column equals its own single solve to the tolerance's accuracy and all
