@@ -167,12 +167,38 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def source_hash():
+def _definition(path, name):
+    """Source text of the function `name` in `path`: from the start of the
+    statement that declares it (its template line included) to the brace
+    that closes its body."""
+    with open(path) as fh:
+        src = fh.read()
+    i = src.find(" " + name + "(")
+    if i < 0:
+        return ""
+    start = max(src.rfind("\ntemplate", 0, i), src.rfind("\nvoid", 0, i), src.rfind("\n}", 0, i) + 2)
+    j = src.find("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            return src[start:k + 1]
+    return src[start:]
+
+
+# kernel -> (file, function) pairs whose text decides the DRAM traffic of a launch
+TRAFFIC_SOURCES = {
+    "ic0_apply": [("solver_kernels.cuh", "k_trsv_level_packed"), ("setup.cpp", "build_packed")],
+}
+
+
+def source_hash(kernel="ic0_apply"):
+    """Hash of the source of the kernel (and of the layout it reads) whose
+    ncu traffic is recorded; a change there invalidates the record."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1309_5048_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(name.encode() + fh.read())
+    for fname, func in TRAFFIC_SOURCES[kernel]:
+        h.update(_definition(os.path.join(csrc, fname), func).encode())
     return h.hexdigest()[:16]
 
 
@@ -187,7 +213,7 @@ def traffic_for(kernel, workload, trsv=None, precision=None):
     except (OSError, ValueError):
         return None
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("src_hash") != source_hash():
+    if not e or kernel not in TRAFFIC_SOURCES or e.get("src_hash") != source_hash(kernel):
         return None
     if e.get("trsv", trsv) != trsv or e.get("precision", precision) != precision:
         return None
