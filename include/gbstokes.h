@@ -4,9 +4,14 @@
  * (Raviart-Thomas type) B-spline discretisation of Stokes flow on the unit
  * square or cube with Nitsche no-slip terms (Sec. 3.2, Sec. 4), solved by
  * preconditioned MINRES (Sec. 5) with the block-diagonal preconditioner
- * diag(M_A, M_Q) of Sec. 5.1: M_A^{-1} is a relaxed inner conjugate-gradient
- * solve on A_h preconditioned by incomplete Cholesky IC(0) (Sec. 6.4), and
- * M_Q = Diag(Q_nu), Q_nu = Q / (2 nu) (Sec. 5.1).
+ * diag(M_A, M_Q) of Sec. 5.1.  By default M_A^{-1} is a relaxed inner
+ * conjugate-gradient solve on A_h preconditioned by incomplete Cholesky IC(0)
+ * (Sec. 6.4) and M_Q = Diag(Q_nu), Q_nu = Q / (2 nu) (Sec. 5.1); the other
+ * blocks of Sec. 5.1 (Diag(A), diagonally preconditioned CG on A_h or Q, and
+ * the IC(0)-preconditioned CG on Q of Sec. 6.4) are options of gb_solve.  The
+ * loads of the manufactured solution (Sec. 6.2), the lid-driven cavity
+ * (Sec. 6.4) and a Fourier forcing, an adjoint solve and Ritz-value
+ * diagnostics of the MINRES Lanczos process are provided.
  *
  * Conventions shared by every entry point
  * ---------------------------------------

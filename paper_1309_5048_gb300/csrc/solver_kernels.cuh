@@ -3,7 +3,9 @@
 // Sec. 5: MINRES on K x = b, K = [A_h B^T; B 0], with the block-diagonal
 // preconditioner M = diag(M_A, M_Q) (eq. general_precond_M): M_A^{-1} r is a
 // relaxed inner conjugate-gradient solve with A_h preconditioned by IC(0)
-// (Sec. 6.4, "PCG(A)"), M_Q = Diag(Q_nu) with Q_nu = Q / (2 nu) (Sec. 5.1).
+// (Sec. 6.4, "PCG(A)") or by its diagonal, or Diag(A_h); M_Q = Diag(Q_nu)
+// with Q_nu = Q / (2 nu) (Sec. 5.1), or a CG solve with Q_nu preconditioned by
+// the exact IC(0) factor of Q or by its diagonal.
 // MINRES is the Lanczos process in the M^{-1} inner product with a QR
 // factorisation of the tridiagonal matrix by Givens rotations (eq.
 // opt_condition, eq. linsys_precond); |eta| tracks ||r||_{M^{-1}}.
@@ -381,8 +383,9 @@ __global__ void k_lanczos(Args a) {
 // z_{j+1,u} = x_cg (the inner CG result), z_{j+1,p} = 2 nu x_q with the
 // IC(0)-PCG pressure block; gamma_{j+1}^2 = z_{j+1}^T v_{j+1}.
 // j = 0: initial recurrence values.  j >= 1: Givens rotation of the new
-// column of the tridiagonal matrix, coefficient of the x update, new eta and
-// the convergence test |eta| / gamma_1 <= tol.
+// column of the tridiagonal matrix, coefficient of the x update, new eta,
+// the record of T_j, and with the estimate stopping rule the convergence test
+// |eta| / gamma_1 <= tol (the 2-norm rule is tested in k_update).
 template <int K, class T>
 __global__ void k_gamma(Args a) {
   const int j = *a.jcur;
