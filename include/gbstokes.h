@@ -271,7 +271,11 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * entries they need in one round trip; about 4 / 12 / 32 entries per lane),
  * 5 / 6 packed (the staged scheme on a k-major copy of each block, so that a
  * warp gathers the same stencil entry of neighbouring rows; about 12 / 32
- * entries per lane).
+ * entries per lane), 7 / 8 split packed (the packed scheme with each row's
+ * entries split by the level of their column: a level sums the entries of
+ * levels two or more steps back before it waits for the level just before it,
+ * and releases the next level only after that wait; about 12 / 32 entries per
+ * lane).
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside
@@ -299,6 +303,9 @@ int gb_get_batch_sweep(const gb_ctx* ctx, int precision, int width, int* variant
  *           triangular solve over all levels (2 x levels launches)
  *        2: Stokes operator product K z with its reduction (one kernel)
  *        3: forward triangular solve over all levels (levels launches)
+ * Before each timed sweep (which 1, 3) an untimed inner CG product runs, so
+ * that the factor is read with the L2 contents of a solve (where A_h streams
+ * through L2 between preconditioner applications), not from a warm L2.
  * The buffers of the last solve are reused and overwritten (its returned
  * solution is not touched).  GB_ERR_INVALID_ARG before any solve. */
 int gb_time_kernel(gb_ctx* ctx, int which, int reps, double* ms_host);

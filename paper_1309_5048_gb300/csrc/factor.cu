@@ -155,6 +155,8 @@ int64_t factor_ic0(Ctx& c) {
   sell_refill(c, c.sU, c.U_val.p);
   sell_refill(c, c.pL.data, c.L_val.p);
   sell_refill(c, c.pU.data, c.U_val.p);
+  sell_refill(c, c.qL.data, c.L_val.p);
+  sell_refill(c, c.qU.data, c.U_val.p);
   GBS_CUDA(cudaMemcpyAsync(c.status_d.p + 1, &init, sizeof(int), cudaMemcpyHostToDevice, c.stream));
   k_band_cholesky<<<1, 32, 0, c.stream>>>(c.N + c.p - 1, c.p, c.q1.p, c.l1.p, c.l1_32.p, c.status_d.p + 1);
   GBS_CUDA(cudaGetLastError());

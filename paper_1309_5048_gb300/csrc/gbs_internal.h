@@ -108,7 +108,11 @@ struct Staged {
 // reading consecutive slots reads the same stencil entry of consecutive rows.
 // desc[4b .. 4b+3] = {first row, rows, first slot, slots per row}; level l owns
 // blocks lev_b[l] .. lev_b[l] + lev_nb[l] - 1.  data.src maps slots to CSR
-// positions (-1 for padding) to refill values after factorisation.
+// positions (-1 for padding) to refill values after factorisation.  The split
+// copies (Ctx::qL, qU) put the entries whose column lies in the level swept
+// just before in a second k-major segment of rows * lr slots after the first
+// rows * lo; their desc.w is lo + (lr << 16) and lev_mean counts the first
+// segment only.
 constexpr int kPackedSlots = 2048;
 struct Packed {
   Sell data;  // col, src, val, val32, slots (off / row0 / rowlen unused)
@@ -223,6 +227,7 @@ struct Ctx {
   std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
   Staged tL, tU;                   // staged-sweep partitions of L and U = L^T
   Packed pL, pU;                   // packed (k-major) copies of L and U
+  Packed qL, qU;                   // the same, each row split by the level of its columns
   int n_sm = 0;                    // streaming multiprocessors of the device
   // kernel layout per precision (index 0 FP64, 1 mixed) for single-RHS
   // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row,

@@ -367,29 +367,54 @@ void build_staged(const std::vector<int32_t>& ptr, const std::vector<int32_t>& l
 // Packed k-major copy of each level of a sweep over the CSR pattern (ptr,
 // col) for the packed kernels (Packed in gbs_internal.h).  Blocks are cut as
 // in build_staged, with the padded size rows * (longest row) as the cap.
+// With split = +1 (forward sweep) or -1 (backward sweep) every row's entries
+// are divided by the level of their column: the entries of the level the
+// sweep finished just before (l - split) form a second k-major segment after
+// the others, and a block's padded size is rows * (longest first part +
+// longest second part).  desc.w then holds lo + (lr << 16).
 void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
-                  const std::vector<int32_t>& lev_ptr, int n_sm, Packed& T, cudaStream_t stream) {
+                  const std::vector<int32_t>& lev_ptr, int n_sm, Packed& T, cudaStream_t stream,
+                  int split = 0) {
   const int nlev = (int)lev_ptr.size() - 1;
   std::vector<int32_t> desc, pcol, psrc;
+  std::vector<int32_t> lev_of;
+  if (split) {
+    lev_of.assign(lev_ptr[nlev], 0);
+    for (int l = 0; l < nlev; ++l)
+      for (int32_t r = lev_ptr[l]; r < lev_ptr[l + 1]; ++r) lev_of[r] = l;
+  }
   T.lev_b.assign(nlev, 0);
   T.lev_nb.assign(nlev, 0);
   T.lev_mean.assign(nlev, 0.f);
   T.cap = T.rcap = 0;
-  auto emit = [&](int32_t rb, int32_t nr, int32_t len) {
+  // entries of row r in the second segment (0 without a split)
+  auto recent = [&](int32_t r, int l) {
+    if (!split) return 0;
+    int32_t m = 0;
+    for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) m += lev_of[col[e]] == l - split;
+    return (int)m;
+  };
+  auto emit = [&](int l, int32_t rb, int32_t nr, int32_t lo, int32_t lr) {
     const int64_t off = (int64_t)pcol.size();
+    const int64_t len = (int64_t)lo + lr;
     if (off + (int64_t)nr * len >= INT32_MAX) fail(GB_ERR_INVALID_ARG, "packed copy exceeds 32-bit indexing");
     desc.push_back(rb);
     desc.push_back(nr);
     desc.push_back((int32_t)off);
-    desc.push_back(len);
+    desc.push_back(lo + (lr << 16));
     pcol.resize(off + (int64_t)nr * len, -1);
     psrc.resize(off + (int64_t)nr * len, -1);
-    for (int32_t i = 0; i < nr; ++i)
-      for (int32_t k = 0; k < ptr[rb + i + 1] - ptr[rb + i]; ++k) {
-        pcol[off + (int64_t)k * nr + i] = col[ptr[rb + i] + k];
-        psrc[off + (int64_t)k * nr + i] = ptr[rb + i] + k;
+    for (int32_t i = 0; i < nr; ++i) {
+      int32_t ko = 0, kr = 0;
+      for (int32_t e = ptr[rb + i]; e < ptr[rb + i + 1]; ++e) {
+        const bool second = split && lev_of[col[e]] == l - split;
+        const int64_t slot = second ? off + (int64_t)nr * lo + (int64_t)(kr++) * nr + i
+                                    : off + (int64_t)(ko++) * nr + i;
+        pcol[slot] = col[e];
+        psrc[slot] = e;
       }
-    T.cap = std::max(T.cap, nr * len);
+    }
+    T.cap = std::max<int>(T.cap, (int)(nr * len));
     T.rcap = std::max(T.rcap, nr);
   };
   for (int l = 0; l < nlev; ++l) {
@@ -399,27 +424,31 @@ void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& c
     nb = nb <= n_sm ? std::min<int64_t>(R, n_sm) : (nb + n_sm - 1) / n_sm * n_sm;
     const double share = (double)(E + 4 * R) / (double)std::max<int64_t>(1, nb);
     T.lev_b[l] = (int32_t)(desc.size() / 4);
-    T.lev_mean[l] = R ? (float)((double)E / (double)R) : 0.f;
-    int32_t rb = r0, rows = 0, len = 0, cuts = 0;
+    int64_t first = 0;  // entries of the level in the first segment
+    int32_t rb = r0, rows = 0, lo = 0, lr = 0, cuts = 0;
     int64_t acc = 0;
     for (int32_t r = r0; r < r1; ++r) {
-      const int32_t lr = ptr[r + 1] - ptr[r];
-      if (lr > kPackedSlots) fail(GB_ERR_INVALID_ARG, "row too long for the packed sweep");
-      const bool full = (int64_t)(rows + 1) * std::max(len, lr) > kPackedSlots || rows == kStagedRows;
-      const bool due = rows > 0 && (double)(acc + lr + 4) > share * (double)(cuts + 1);
+      const int32_t len = ptr[r + 1] - ptr[r];
+      const int32_t m = recent(r, l);
+      first += len - m;
+      if (len > kPackedSlots) fail(GB_ERR_INVALID_ARG, "row too long for the packed sweep");
+      const bool full =
+          (int64_t)(rows + 1) * (std::max(lo, len - m) + std::max(lr, m)) > kPackedSlots || rows == kStagedRows;
+      const bool due = rows > 0 && (double)(acc + len + 4) > share * (double)(cuts + 1);
       if (rows > 0 && (full || due)) {
-        emit(rb, rows, len);
+        emit(l, rb, rows, lo, lr);
         ++cuts;
         rb = r;
-        rows = 0;
-        len = 0;
+        rows = lo = lr = 0;
       }
-      acc += lr + 4;
-      len = std::max(len, lr);
+      acc += len + 4;
+      lo = std::max(lo, len - m);
+      lr = std::max(lr, m);
       ++rows;
     }
-    emit(rb, rows, len);
+    emit(l, rb, rows, lo, lr);
     T.lev_nb[l] = cuts + 1;
+    T.lev_mean[l] = R ? (float)((double)first / (double)R) : 0.f;
   }
   T.desc.upload(desc.data(), desc.size(), stream);
   Sell& S = T.data;
@@ -676,6 +705,8 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   build_staged(Uptr, c.lev_ptr, c.n_sm, c.tU, s);
   build_packed(Lptr, Lcol, c.lev_ptr, c.n_sm, c.pL, s);
   build_packed(Uptr, Ucol, c.lev_ptr, c.n_sm, c.pU, s);
+  build_packed(Lptr, Lcol, c.lev_ptr, c.n_sm, c.qL, s, +1);
+  build_packed(Uptr, Ucol, c.lev_ptr, c.n_sm, c.qU, s, -1);
   c.max_lrow = 0;
   for (int64_t r = 0; r < n; ++r)
     c.max_lrow = std::max({c.max_lrow, Lptr[r + 1] - Lptr[r], Uptr[r + 1] - Uptr[r]});

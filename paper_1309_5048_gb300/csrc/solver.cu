@@ -226,6 +226,24 @@ void packed_allow_smem(size_t bytes) {
   packed_allow_smem_one<T, FWD, 32>(bytes);
 }
 
+template <class T, bool FWD, int G>
+void split_allow_smem_one(size_t bytes) {
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_split<T, FWD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes));
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_split<T, FWD, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+}
+
+template <class T, bool FWD>
+void split_allow_smem(size_t bytes) {
+  split_allow_smem_one<T, FWD, 1>(bytes);
+  split_allow_smem_one<T, FWD, 2>(bytes);
+  split_allow_smem_one<T, FWD, 4>(bytes);
+  split_allow_smem_one<T, FWD, 8>(bytes);
+  split_allow_smem_one<T, FWD, 16>(bytes);
+  split_allow_smem_one<T, FWD, 32>(bytes);
+}
+
 // Dynamic shared memory of k_trsv_level_packed (one size for every launch).
 size_t packed_smem_bytes(int cap, int rcap, size_t tsize) {
   return (size_t)(2 * cap + 2 * rcap) * tsize + (size_t)cap * 4;
@@ -234,6 +252,13 @@ size_t packed_smem_bytes(int cap, int rcap, size_t tsize) {
 template <class T>
 size_t packed_bytes(const Ctx& c) {
   return packed_smem_bytes(std::max(c.pL.cap, c.pU.cap), std::max(c.pL.rcap, c.pU.rcap), sizeof(T));
+}
+
+// Dynamic shared memory of k_trsv_level_split (one size for every launch):
+// values and solution entries per slot, partial sum and inverse diagonal per row.
+template <class T>
+size_t split_bytes(const Ctx& c) {
+  return (size_t)(2 * std::max(c.qL.cap, c.qU.cap) + 2 * std::max(c.qL.rcap, c.qU.rcap)) * sizeof(T);
 }
 
 template <class T, bool FWD>
@@ -278,6 +303,8 @@ void staged_prepare(Ctx& c) {
   staged_allow_smem<T, false>(staged_bytes<T>(c));
   packed_allow_smem<T, true>(packed_bytes<T>(c));
   packed_allow_smem<T, false>(packed_bytes<T>(c));
+  split_allow_smem<T, true>(split_bytes<T>(c));
+  split_allow_smem<T, false>(split_bytes<T>(c));
 }
 
 template <class T>
@@ -330,8 +357,42 @@ struct Run {
                                 (const int32_t*)pk.data.col.p, pick_host<T>(pk.data.val.p, pk.data.val32.p),
                                 std::max(c.pL.cap, c.pU.cap), std::max(c.pL.rcap, c.pU.rcap)));
   }
+  template <bool FWD, int GG>
+  void split_level(cudaLaunchConfig_t& cfg, const Packed& pk, int l) {
+    const int ln = FWD ? l + 1 : l - 1;  // next level of the sweep
+    const bool has = ln >= 0 && ln < c.nlev;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_split<T, FWD, GG>, a, (const int4*)pk.desc.p + pk.lev_b[l],
+                                (const int32_t*)pk.data.col.p, pick_host<T>(pk.data.val.p, pk.data.val32.p),
+                                std::max(c.qL.cap, c.qU.cap), std::max(c.qL.rcap, c.qU.rcap),
+                                (const int4*)pk.desc.p + (has ? pk.lev_b[ln] : 0), has ? pk.lev_nb[ln] : 0));
+  }
   template <bool FWD>
   void level(int l) {
+    if (K == 1 && vtrsv >= 7) {
+      const Packed& pk = FWD ? c.qL : c.qU;
+      const float per_lane = vtrsv == 7 ? 12.f : 32.f;
+      int lanes = 1;
+      while (lanes < 32 && pk.lev_mean[l] > per_lane * (float)lanes) lanes *= 2;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)pk.lev_nb[l]);
+      cfg.blockDim = dim3(kBlock);
+      cfg.dynamicSmemBytes = split_bytes<T>(c);
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      switch (lanes) {
+        case 1: split_level<FWD, 1>(cfg, pk, l); break;
+        case 2: split_level<FWD, 2>(cfg, pk, l); break;
+        case 4: split_level<FWD, 4>(cfg, pk, l); break;
+        case 8: split_level<FWD, 8>(cfg, pk, l); break;
+        case 16: split_level<FWD, 16>(cfg, pk, l); break;
+        default: split_level<FWD, 32>(cfg, pk, l); break;
+      }
+      return;
+    }
     if (K == 1 && vtrsv >= 5) {
       const Packed& pk = FWD ? c.pL : c.pU;
       const float per_lane = vtrsv == 5 ? 12.f : 32.f;
@@ -626,8 +687,9 @@ struct Run {
 // Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
 // SELL-32 (thread per row; 2 or 4 warps per slice) forms of the inner SpMV,
 // and the CSR, SELL-32,
-// three staged (about 4, 12, 32 entries per lane) and two packed (about 12,
-// 32 entries per lane) forms of one IC(0) application, on this problem, and
+// three staged (about 4, 12, 32 entries per lane), two packed and two split
+// packed (about 12, 32 entries per lane) forms of one IC(0) application, on
+// this problem, and
 // keep the fastest; a form replaces the
 // best so far only when it is 3% faster.  Runs once per precision, outside
 // any graph capture; the choice only changes the summation order inside a row.
@@ -651,21 +713,32 @@ void autotune_single(Ctx& c) {
     if (which == 0) run.vspmv = variant;
     else run.vtrsv = variant;
     const int reps = which == 0 ? 20 : 5;
-    auto launch = [&] {
-      if (which == 0) run.spmv();
-      else {
-        run.trsv_fwd();
-        run.trsv_bwd();
-      }
-    };
-    launch();
-    GBS_CUDA(cudaEventRecord(e0, c.stream));
-    for (int r = 0; r < reps; ++r) launch();
-    GBS_CUDA(cudaEventRecord(e1, c.stream));
-    GBS_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    return ms;
+    if (which == 0) {
+      run.spmv();
+      GBS_CUDA(cudaEventRecord(e0, c.stream));
+      for (int r = 0; r < reps; ++r) run.spmv();
+      GBS_CUDA(cudaEventRecord(e1, c.stream));
+      GBS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms;
+    }
+    // an IC(0) application, each after an untimed SpMV that streams A_h
+    // through L2 as in the solve (back-to-back sweeps would find the factor
+    // in L2 and favour the forms that prefetch least)
+    float total = 0.f;
+    for (int r = 0; r <= reps; ++r) {
+      run.spmv();
+      GBS_CUDA(cudaEventRecord(e0, c.stream));
+      run.trsv_fwd();
+      run.trsv_bwd();
+      GBS_CUDA(cudaEventRecord(e1, c.stream));
+      GBS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) total += ms;
+    }
+    return total;
   };
   if (c.var_spmv[pi] < 0) {
     float best = time_it(0, 0);
@@ -682,7 +755,7 @@ void autotune_single(Ctx& c) {
   if (c.var_trsv[pi] < 0) {
     float best = time_it(0, 1);
     int choice = 0;
-    for (int v = 1; v <= 6; ++v) {
+    for (int v = 1; v <= 8; ++v) {
       const float t = time_it(v, 1);
       if (t < 0.97f * best) {
         best = t;
@@ -824,6 +897,9 @@ double time_family(Ctx& c, int which, int reps) {
   std::vector<cudaEvent_t> ev(2 * reps);
   for (auto& e : ev) GBS_CUDA(cudaEventCreate(&e));
   for (int r = 0; r < reps; ++r) {
+    // sweeps: the inner SpMV runs untimed before each one and streams A_h
+    // through L2, as it does before every preconditioner application of a solve
+    if (which == 1 || which == 3) run.spmv();
     GBS_CUDA(cudaEventRecord(ev[2 * r], c.stream));
     launch();
     GBS_CUDA(cudaEventRecord(ev[2 * r + 1], c.stream));

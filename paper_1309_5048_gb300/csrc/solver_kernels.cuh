@@ -1126,6 +1126,117 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_packed(Args a, const int4
   }
 }
 
+// Packed sweep level on the split copy (Packed, Ctx::qL / qU): each row's
+// entries whose column lies two or more levels back in the sweep come first,
+// those of the level just before it in a second segment.  The launch signals
+// its dependent level only after its own wait has returned, i.e. after the
+// level before it has completed.  So when a level's blocks start, every level
+// two or more steps back has completed and its stores are visible at device
+// scope: the blocks gather those solution entries (L2 loads) and sum the first
+// segment before they wait, and after the wait gather only the second segment
+// and finish the rows (Sec. 6.4, "PCG(A)": the IC(0) application).  The
+// wait is the programmatic dependency on the preceding launch alone.  Only
+// two levels are in flight at a time, so each launch first asks L2 to fetch
+// the columns and values of the next level of the sweep (next[0 .. nnext)),
+// whose blocks start after this level's wait.
+template <class T, bool FWD, int G>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_split(Args a, const int4* __restrict__ desc,
+                                                             const int32_t* __restrict__ pcol,
+                                                             const T* __restrict__ pval, int cap, int rcap,
+                                                             const int4* __restrict__ next, int nnext) {
+  constexpr int EPT = kPackedSlots / kBlock;  // slots per thread
+  static_assert(EPT * kBlock == kPackedSlots && kStagedRows <= kBlock, "packed block shape");
+  extern __shared__ __align__(16) unsigned char split_smem[];
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  T* sv = (T*)split_smem;  // first segment: values
+  T* sx = sv + cap;        // first segment: solution entries; second: products
+  T* ss = sx + cap;        // per row: sum over the first segment
+  T* si = ss + rcap;       // per row: inverse diagonal
+  const int tid = threadIdx.x;
+  for (int b = blockIdx.x; b < nnext; b += gridDim.x) {
+    const int4 e = next[b];
+    const int n2 = e.y * ((e.w & 0xffff) + (e.w >> 16));  // slots of that block
+    constexpr int VL = 128 / (int)sizeof(T);               // values per 128-byte line
+    const int lc = (n2 + 31) / 32, lv = (n2 + VL - 1) / VL;
+    for (int t = tid; t < lc + lv; t += kBlock) {
+      const void* p = t < lc ? (const void*)(pcol + e.z + 32 * t) : (const void*)(pval + e.z + VL * (t - lc));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+    }
+  }
+  const int4 d = desc[blockIdx.x];
+  const int rb = d.x, nr = d.y, off = d.z, lo = d.w & 0xffff, lr = d.w >> 16;
+  const int no = nr * lo, ns = no + nr * lr;
+  int cv[EPT];
+  T vv[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int q = tid + u * kBlock;
+    cv[u] = q < ns ? pcol[off + q] : -1;
+    vv[u] = q < ns ? pval[off + q] : T(0);
+  }
+  {
+    T xv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      xv[u] = (q < no && cv[u] >= 0) ? __ldcg(out + cv[u]) : T(0);
+    }
+    const T iv = tid < nr ? inv[rb + tid] : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      if (q < no) {
+        sv[q] = vv[u];
+        sx[q] = xv[u];
+      }
+    }
+    if (tid < nr) si[tid] = iv;
+  }
+  __syncthreads();
+  const int g = tid % G;
+  for (int i = tid / G; i < nr; i += kBlock / G) {  // uniform over a lane group
+    T s0 = 0, s1 = 0;
+    int k = g;
+    for (; k + G < lo; k += 2 * G) {
+      s0 += sv[k * nr + i] * sx[k * nr + i];
+      s1 += sv[(k + G) * nr + i] * sx[(k + G) * nr + i];
+    }
+    if (k < lo) s0 += sv[k * nr + i] * sx[k * nr + i];
+    T s = s0 + s1;
+    if (G > 1) {
+      if (sizeof(T) == 8) s = (T)group_sum<G>((double)s);
+      else s = (T)group_sumf<G>((float)s);
+    }
+    if (g == 0) ss[i] = s;
+  }
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // read with the gathers; decides the stores
+  {
+    T xv[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      xv[u] = (q >= no && q < ns && cv[u] >= 0) ? __ldcg(out + cv[u]) : T(0);
+    }
+    const T rv = tid < nr ? __ldcg(rhs + rb + tid) : T(0);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int q = tid + u * kBlock;
+      if (q >= no && q < ns) sx[q] = vv[u] * xv[u];
+    }
+    __syncthreads();
+    if (!live) return;
+    if (tid < nr) {
+      T s = ss[tid];
+      for (int k = 0; k < lr; ++k) s += sx[no + k * nr + tid];
+      out[rb + tid] = (rv - s) * si[tid];
+    }
+  }
+}
+
 // x[i] = v (kernel timing and layout tuning only).
 template <class T>
 __global__ void k_fill_value(T* __restrict__ x, int64_t n, T v) {

@@ -327,7 +327,7 @@ def test_edge_cases(oracle_mod, gb):
 
 LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr"), ("csr", "staged4"),
                 ("sell", "staged12"), ("csr", "staged32"), ("csr", "packed12"), ("sell", "packed32"),
-                ("sell2w", "packed32"), ("sell4w", "csr")]
+                ("sell2w", "packed32"), ("sell4w", "csr"), ("csr", "split12"), ("sell2w", "split32")]
 
 
 @pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
@@ -360,7 +360,7 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     s.solve(rhs, tol=1e-6)
     spmv, trsv = s.kernel_variants("fp64")
     assert spmv in ("csr", "sell", "sell2w", "sell4w") and trsv in ("csr", "sell", "staged4", "staged12", "staged32", "packed12",
-                                                 "packed32")
+                                                 "packed32", "split12", "split32")
 
 
 @pytest.mark.slow
