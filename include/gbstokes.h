@@ -158,8 +158,10 @@ int gb_setup_pattern(const gb_problem* prob, void* stream, gb_ctx** out);
 
 /* out[0..9] = n_u, n_p, nnz(A_h), nnz(B), nnz(L) (IC(0) factor incl. diagonal),
  * number of forward levels, number of backward levels, nnz(Q) (structural),
- * bytes of device memory held by the context, number of colours used by the
- * ordering (0 unless multicolour). */
+ * bytes of device memory held by the context for the operators, the factors
+ * and their kernel layouts at the time of the call (the solve workspace is
+ * not counted), number of colours used by the ordering (0 unless
+ * multicolour). */
 int gb_sizes(const gb_ctx* ctx, int64_t* out_host);
 
 /* Assembles A_h = a - eta_h, B and Diag(Q) (Sec. 4: [A_h]_ij = a_h(Phi_j,Phi_i),

@@ -146,7 +146,7 @@ int gb_sizes(const gb_ctx* h, int64_t* out) {
   out[5] = c.nlev;
   out[6] = c.nrlev;
   out[7] = c.nnzQ;
-  out[8] = (int64_t)c.device_bytes;
+  out[8] = (int64_t)held_bytes(c);
   out[9] = c.ncolours;
   return GB_OK;
 }

@@ -244,11 +244,12 @@ struct Ctx {
   double nu = 1.0, cpen = 0.0;
   bool assembled = false, factored = false;
   Workspace ws;
-  size_t device_bytes = 0;
 };
 
 // setup.cpp
 void setup_pattern(Ctx& c, const gb_problem& prob);
+// Device bytes of the context's operators, factors and kernel layouts.
+size_t held_bytes(const Ctx& c);
 // assemble.cu
 void assemble(Ctx& c, double nu, double cpen);
 void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, double* f_dev);

@@ -713,9 +713,34 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   c.status_d.alloc(16);
   c.status_d.zero(s);
   GBS_CUDA(cudaStreamSynchronize(s));
-  c.device_bytes = (size_t)(n + 1) * 4 * 4 + (size_t)c.nnzA * (4 + 8 + 4) + n * 4 * 3 +
-                   Lcol.size() * (4 + 8 + 4) + Ucol.size() * (4 + 4 + 8 + 4) + n * 8 * 3 +
-                   (size_t)c.nnzB * (4 * 3 + 8 * 2) + np * 16 + (size_t)c.nnzQ * (4 + 8 + 4) + np * 4;
+}
+
+namespace {
+template <class T>
+size_t bytes_of(const DevBuf<T>& b) {
+  return b.p ? b.n * sizeof(T) : 0;
+}
+size_t bytes_of(const Sell& s) {
+  return bytes_of(s.off) + bytes_of(s.row0) + bytes_of(s.rowlen) + bytes_of(s.col) + bytes_of(s.src) +
+         bytes_of(s.val) + bytes_of(s.val32);
+}
+size_t bytes_of(const Packed& p) { return bytes_of(p.data) + bytes_of(p.desc); }
+}  // namespace
+
+size_t held_bytes(const Ctx& c) {
+  size_t b = bytes_of(c.order_d) + bytes_of(c.iorder_d) + bytes_of(c.pos_d);
+  b += bytes_of(c.A_ptr) + bytes_of(c.A_col) + bytes_of(c.A_diag) + bytes_of(c.A_val) + bytes_of(c.A_val32);
+  b += bytes_of(c.L_ptr) + bytes_of(c.L_col) + bytes_of(c.L_val) + bytes_of(c.L_diag) + bytes_of(c.L_inv) +
+       bytes_of(c.L_val32) + bytes_of(c.L_inv32);
+  b += bytes_of(c.U_ptr) + bytes_of(c.U_col) + bytes_of(c.U_map) + bytes_of(c.U_val) + bytes_of(c.U_val32);
+  b += bytes_of(c.B_ptr) + bytes_of(c.B_col) + bytes_of(c.Bt_ptr) + bytes_of(c.Bt_col) + bytes_of(c.Bt_map) +
+       bytes_of(c.B_val) + bytes_of(c.Bt_val);
+  b += bytes_of(c.Qdiag) + bytes_of(c.wmean) + bytes_of(c.tab1d);
+  b += bytes_of(c.Q_ptr) + bytes_of(c.Q_col) + bytes_of(c.Q_val) + bytes_of(c.Q_val32) + bytes_of(c.q1) +
+       bytes_of(c.l1) + bytes_of(c.l1_32);
+  b += bytes_of(c.sA) + bytes_of(c.sL) + bytes_of(c.sU) + bytes_of(c.tL.desc) + bytes_of(c.tU.desc);
+  b += bytes_of(c.pL) + bytes_of(c.pU) + bytes_of(c.qL) + bytes_of(c.qU) + bytes_of(c.status_d);
+  return b;
 }
 
 }  // namespace gbs
