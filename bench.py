@@ -236,6 +236,32 @@ def algorithmic_bytes(s, kernel, precision, k):
     raise ValueError(kernel)
 
 
+def cg_vector_bytes(s, precision):
+    """Vector bytes of one inner CG iteration beyond its SpMV and IC(0)
+    application: nine n_u-vector reads or writes (x and r updates, r^T z,
+    p update)."""
+    return 9 * (4 if precision == "mixed" else 8) * s.n_u
+
+
+def minres_vector_bytes(s):
+    """FP64 vector bytes of one MINRES step beyond its Stokes product and
+    preconditioner application: fourteen (n_u + n_p)-vector reads or writes
+    (Lanczos, rotation, w and x updates) and three n_p ones (Diag(Q) scaling,
+    zero-mean pressure)."""
+    return 14 * 8 * (s.n_u + s.n_p) + 3 * 8 * s.n_p
+
+
+def solve_bytes(s, info, precision):
+    """Algorithmic bytes of one single-RHS solve with the Diag(Q) pressure
+    block, from its measured counts: outer + 1 Stokes products, one IC(0)
+    application per preconditioner application and per inner iteration, one
+    SpMV per inner iteration, and the vector work of both loops."""
+    return ((info["outer_its"] + 1) * algorithmic_bytes(s, "stokes_apply", precision, 1)
+            + (info["precond_apps"] + info["inner_its_total"]) * algorithmic_bytes(s, "ic0_apply", precision, 1)
+            + info["inner_its_total"] * (algorithmic_bytes(s, "cg_spmv", precision, 1) + cg_vector_bytes(s, precision))
+            + info["outer_its"] * minres_vector_bytes(s))
+
+
 def launches_per_solve(s, info, pressure="diag"):
     """Kernel launches of one solve as the graph driver issues them (the
     pressure CG adds, per application, dim line-solve passes and a rho
@@ -443,6 +469,14 @@ def main():
             "unit_of_launch": ("one preconditioner application: forward + backward IC(0) sweep over %d levels "
                                "each" % s.nlevels) if dom == "ic0_apply" else "one kernel launch"}
     del x_last
+    # the whole solve against the same peak: algorithmic bytes from the
+    # measured counts over the measured time per solve (k = 1, Diag(Q) only)
+    whole = None
+    if k == 1 and args.pressure == "diag":
+        sb = solve_bytes(s, infos[0], args.precision)
+        gbs = sb / (ms / args.steps * 1e-3) / 1e9
+        whole = {"bytes_per_solve": sb, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                 "peak_source": peak_kind}
 
     variants = {}
     if not args.no_variants and rank == 0:
@@ -482,6 +516,7 @@ def main():
                        "l2": "no flush: per-iteration working set (A, L, L^T, vectors) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
+            "solve_roofline": whole,
             "cpu_baseline": cpu,
             "e2e": {"value": throughput(world, args.steps, k, 1000.0 * e2e_s), "unit": "solves/s",
                     "h2d_bytes_per_step": bytes_io,
