@@ -1,4 +1,4 @@
-"""GPU spectral diagnostics (SURVEY NEXT-4): the Lanczos tridiagonal recorded
+"""GPU spectral diagnostics: the Lanczos tridiagonal recorded
 by the device MINRES equals the oracle's under replay, and the library's
 host-side bisection (gb_ritz_extremes) gives the eigenvalues of that
 tridiagonal; at h = 1/32 they reproduce the paper's Table neg_and_pos_eig_k_2."""

@@ -6,9 +6,10 @@
   component contributes, l = 2 nu prod_{m != k} int B_{a_m} *
   (-(1/2) B'_{a_k}(1) + (C_pen / h) B_{a_k}(1)).
 * The MINRES counts of Tables niter_cavity_k_2 and ic_pgc_tols_k2 within 15 %
-  (2-norm stop at 1e-12).  The cavity's corner singularity sits where the
-  paper's space has its two extra corner DOFs (reading 2 of the design
-  notes), so exact counts are not expected here (the square-domain tables
+  (2-norm stop at 1e-12).  The paper's velocity space has two more DOFs
+  than the one built here (its size tables exceed the closed-form counts by
+  2), most likely at corners, and the cavity's singularity sits at the lid's
+  corners, so exact counts are not expected here (the square-domain tables
   are pinned exactly).  The mean inner PCG(A) counts are held to 15 % for
   the IC(0) blocks and 25 % for the diagonally preconditioned ones.
   Excluded: PCG(A,Q) at h = 1/8, whose printed mean inner count (14.3) is

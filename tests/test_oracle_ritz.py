@@ -1,5 +1,5 @@
-"""Ritz values of the MINRES Lanczos tridiagonal (SURVEY NEXT-4 spectral
-diagnostics): the eigenvalues of T_j recorded by the oracle's MINRES
+"""Ritz values of the MINRES Lanczos tridiagonal (spectral diagnostics):
+the eigenvalues of T_j recorded by the oracle's MINRES
 approximate the extremal eigenvalues of M^{-1} K.  Pinned against a dense
 generalised eigensolve at h = 1/8 and against the paper's Table
 neg_and_pos_eig_k_2 (Sec. 6.4, h = 1/32, the eigenvalues 0 and 1 disregarded)."""
