@@ -281,7 +281,10 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside
- * these ranges return GB_ERR_INVALID_ARG.  gb_get_kernel_variants reports the
+ * these ranges return GB_ERR_INVALID_ARG, and so do trsv 2 - 8 when a row of
+ * the factor has more than 2048 off-diagonal entries (3D with velocity degree
+ * 5 or 6 on all but the coarsest meshes): those layouts are then not built,
+ * and the automatic choice skips them.  gb_get_kernel_variants reports the
  * current choice (-1: not made). */
 int gb_set_kernel_variants(gb_ctx* ctx, int precision, int spmv, int trsv);
 int gb_get_kernel_variants(const gb_ctx* ctx, int precision, int* spmv, int* trsv);

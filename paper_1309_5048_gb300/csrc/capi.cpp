@@ -253,6 +253,10 @@ int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
     set_error("bad kernel variant request");
     return GB_ERR_INVALID_ARG;
   }
+  if (!gbs::trsv_available(h->c, trsv)) {
+    set_error("sweep layout unavailable: a row of the IC(0) factor does not fit one block");
+    return GB_ERR_INVALID_ARG;
+  }
   h->c.var_spmv[precision] = spmv;
   h->c.var_trsv[precision] = trsv;
   h->c.ws.graph_valid = false;

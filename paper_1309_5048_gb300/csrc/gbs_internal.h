@@ -90,9 +90,13 @@ struct Sell {
 // (a multiple of) the SM count.  Block b of the sweep is described by
 // desc[4b .. 4b+3] = {first row, end row, first entry, end entry} (CSR
 // positions); level l owns blocks lev_b[l] ... lev_b[l] + lev_nb[l] - 1.
+// A factor with a row of more than kStagedEntries off-diagonal entries (3D,
+// velocity degree 5 or 6) gets no partition: ok is false and the staged
+// layouts are unavailable for that problem.
 constexpr int kStagedRows = 256;
 constexpr int kStagedEntries = 2048;
 struct Staged {
+  bool ok = true;
   DevBuf<int32_t> desc;
   std::vector<int32_t> lev_b, lev_nb;
   std::vector<int32_t> lev_ecap, lev_rcap;  // largest block of the level (entries, rows)
@@ -112,9 +116,11 @@ struct Staged {
 // copies (Ctx::qL, qU) put the entries whose column lies in the level swept
 // just before in a second k-major segment of rows * lr slots after the first
 // rows * lo; their desc.w is lo + (lr << 16) and lev_mean counts the first
-// segment only.
+// segment only.  As for Staged, a row longer than kPackedSlots leaves the
+// copy empty with ok false.
 constexpr int kPackedSlots = 2048;
 struct Packed {
+  bool ok = true;
   Sell data;  // col, src, val, val32, slots (off / row0 / rowlen unused)
   DevBuf<int32_t> desc;
   std::vector<int32_t> lev_b, lev_nb;
@@ -250,6 +256,10 @@ struct Ctx {
 void setup_pattern(Ctx& c, const gb_problem& prob);
 // Device bytes of the context's operators, factors and kernel layouts.
 size_t held_bytes(const Ctx& c);
+// Whether single-RHS sweep layout v (gb_set_kernel_variants) exists for this
+// problem: the staged (2-4), packed (5-6) and split packed (7-8) forms need
+// every row of L and U to fit one block.
+bool trsv_available(const Ctx& c, int v);
 // assemble.cu
 void assemble(Ctx& c, double nu, double cpen);
 void load_fourier(Ctx& c, int nmodes, const int32_t* kappa, const double* amp, double* f_dev);

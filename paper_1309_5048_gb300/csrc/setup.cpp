@@ -322,6 +322,10 @@ void build_staged(const std::vector<int32_t>& ptr, const std::vector<int32_t>& l
   T.lev_rcap.assign(nlev, 0);
   T.lev_mean.assign(nlev, 0.f);
   T.ecap = T.rcap = 0;
+  T.ok = true;
+  for (int32_t r = lev_ptr[0]; r < lev_ptr[nlev]; ++r)
+    if (ptr[r + 1] - ptr[r] > kStagedEntries) T.ok = false;
+  if (!T.ok) return;
   for (int l = 0; l < nlev; ++l) {
     const int32_t r0 = lev_ptr[l], r1 = lev_ptr[l + 1];
     const int64_t R = r1 - r0, E = (int64_t)ptr[r1] - ptr[r0];
@@ -387,6 +391,10 @@ void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& c
   T.lev_nb.assign(nlev, 0);
   T.lev_mean.assign(nlev, 0.f);
   T.cap = T.rcap = 0;
+  T.ok = true;
+  for (int32_t r = lev_ptr[0]; r < lev_ptr[nlev]; ++r)
+    if (ptr[r + 1] - ptr[r] > kPackedSlots) T.ok = false;
+  if (!T.ok) return;
   // entries of row r in the second segment (0 without a split)
   auto recent = [&](int32_t r, int l) {
     if (!split) return 0;
@@ -726,6 +734,13 @@ size_t bytes_of(const Sell& s) {
 }
 size_t bytes_of(const Packed& p) { return bytes_of(p.data) + bytes_of(p.desc); }
 }  // namespace
+
+bool trsv_available(const Ctx& c, int v) {
+  if (v >= 2 && v <= 4) return c.tL.ok && c.tU.ok;
+  if (v >= 5 && v <= 6) return c.pL.ok && c.pU.ok;
+  if (v >= 7 && v <= 8) return c.qL.ok && c.qU.ok;
+  return true;
+}
 
 size_t held_bytes(const Ctx& c) {
   size_t b = bytes_of(c.order_d) + bytes_of(c.iorder_d) + bytes_of(c.pos_d);

@@ -756,6 +756,7 @@ void autotune_single(Ctx& c) {
     float best = time_it(0, 1);
     int choice = 0;
     for (int v = 1; v <= 8; ++v) {
+      if (!trsv_available(c, v)) continue;
       const float t = time_it(v, 1);
       if (t < 0.97f * best) {
         best = t;
