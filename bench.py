@@ -168,36 +168,66 @@ def measured_peak():
 
 
 def _definition(path, name):
-    """Source text of the function `name` in `path`: from the start of the
-    statement that declares it (its template line included) to the brace
-    that closes its body."""
+    """Source text of the function `name` in `path`: its definition (an
+    occurrence of `name(` outside a line comment whose parameter list is
+    followed by a body), from the line that declares it (and a template line
+    right above) to the brace that closes its body; "" if there is none."""
     with open(path) as fh:
         src = fh.read()
-    i = src.find(" " + name + "(")
-    if i < 0:
-        return ""
-    start = max(src.rfind("\ntemplate", 0, i), src.rfind("\nvoid", 0, i), src.rfind("\n}", 0, i) + 2)
-    j = src.find("{", i)
-    depth = 0
-    for k in range(j, len(src)):
-        depth += {"{": 1, "}": -1}.get(src[k], 0)
-        if depth == 0:
-            return src[start:k + 1]
-    return src[start:]
+    pos = 0
+    while True:
+        i = src.find(name + "(", pos)
+        if i < 0:
+            return ""
+        pos = i + 1
+        line_start = src.rfind("\n", 0, i) + 1
+        if "//" in src[line_start:i] or (i > 0 and (src[i - 1].isalnum() or src[i - 1] == "_")):
+            continue  # in a comment, or the tail of a longer name
+        k, depth = i + len(name), 0
+        while k < len(src):
+            depth += {"(": 1, ")": -1}.get(src[k], 0)
+            k += 1
+            if depth == 0:
+                break
+        rest = src[k:].lstrip()
+        while rest.startswith("const") or rest.startswith("noexcept"):
+            rest = rest.split(None, 1)[1] if " " in rest else ""
+        if not rest.startswith("{"):
+            continue  # a declaration or a call
+        prev = src.rfind("\n", 0, max(line_start - 1, 0)) + 1
+        start = prev if line_start > 0 and src[prev:line_start].lstrip().startswith("template") else line_start
+        j = src.find("{", k)
+        depth = 0
+        for m in range(j, len(src)):
+            depth += {"{": 1, "}": -1}.get(src[m], 0)
+            if depth == 0:
+                return src[start:m + 1]
+        return src[start:]
 
 
-# kernel -> (file, function) pairs whose text decides the DRAM traffic of a launch
+# (kernel, sweep layout family) -> (file, function) pairs whose text decides
+# the DRAM traffic of a launch
 TRAFFIC_SOURCES = {
-    "ic0_apply": [("solver_kernels.cuh", "k_trsv_level_packed"), ("setup.cpp", "build_packed")],
+    ("ic0_apply", "packed"): [("solver_kernels.cuh", "k_trsv_level_packed"), ("setup.cpp", "build_packed")],
+    ("ic0_apply", "split"): [("solver_kernels.cuh", "k_trsv_level_split"), ("setup.cpp", "build_packed")],
 }
 
 
-def source_hash(kernel="ic0_apply"):
+def _layout_family(trsv):
+    """'packed32' -> 'packed', 'split12' -> 'split' (None stays None)."""
+    return trsv.rstrip("0123456789") if trsv else trsv
+
+
+def source_hash(kernel="ic0_apply", trsv="packed32"):
     """Hash of the source of the kernel (and of the layout it reads) whose
-    ncu traffic is recorded; a change there invalidates the record."""
+    ncu traffic is recorded for this sweep layout; a change there
+    invalidates the record.  None if no sources are registered."""
+    srcs = TRAFFIC_SOURCES.get((kernel, _layout_family(trsv)))
+    if not srcs:
+        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1309_5048_gb300", "csrc")
-    for fname, func in TRAFFIC_SOURCES[kernel]:
+    for fname, func in srcs:
         h.update(_definition(os.path.join(csrc, fname), func).encode())
     return h.hexdigest()[:16]
 
@@ -213,9 +243,10 @@ def traffic_for(kernel, workload, trsv=None, precision=None):
     except (OSError, ValueError):
         return None
     e = d.get(workload, {}).get(kernel)
-    if not e or kernel not in TRAFFIC_SOURCES or e.get("src_hash") != source_hash(kernel):
+    if not e or e.get("trsv") != trsv or e.get("precision") != precision:
         return None
-    if e.get("trsv", trsv) != trsv or e.get("precision", precision) != precision:
+    h = source_hash(kernel, trsv)
+    if h is None or e.get("src_hash") != h:
         return None
     return e.get("dram_bytes_per_launch")
 
