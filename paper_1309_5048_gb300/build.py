@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbstokes.so")
-SOURCES = ["setup.cpp", "assemble.cu", "factor.cu", "solver.cu", "capi.cpp"]
-HEADERS = ["gbs_internal.h", "gbs_device.cuh", "solver_kernels.cuh"]
+SOURCES = ["setup.cpp", "layouts.cpp", "assemble.cu", "factor.cu", "solver.cu", "capi.cpp"]
+HEADERS = ["gbs_internal.h", "gbs_device.cuh", "solver_kernels.cuh", "layouts.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,7 +33,7 @@ def _flags(src: str):
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if src.endswith(".cu"):
         return ARCH + ["-lineinfo", "--expt-relaxed-constexpr"] + common
-    return common + ["-x", "cu"] + ARCH if False else common
+    return common
 
 
 def _stale() -> bool:

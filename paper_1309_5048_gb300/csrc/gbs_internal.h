@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/gbstokes.h"
+#include "layouts.h"
 
 namespace gbs {
 
@@ -92,9 +93,8 @@ struct Sell {
 // positions); level l owns blocks lev_b[l] ... lev_b[l] + lev_nb[l] - 1.
 // A factor with a row of more than kStagedEntries off-diagonal entries (3D,
 // velocity degree 5 or 6) gets no partition: ok is false and the staged
-// layouts are unavailable for that problem.
-constexpr int kStagedRows = 256;
-constexpr int kStagedEntries = 2048;
+// layouts are unavailable for that problem.  Built by staged_layout
+// (layouts.h, which holds the block caps).
 struct Staged {
   bool ok = true;
   DevBuf<int32_t> desc;
@@ -116,9 +116,9 @@ struct Staged {
 // copies (Ctx::qL, qU) put the entries whose column lies in the level swept
 // just before in a second k-major segment of rows * lr slots after the first
 // rows * lo; their desc.w is lo + (lr << 16) and lev_mean counts the first
-// segment only.  As for Staged, a row longer than kPackedSlots leaves the
-// copy empty with ok false.
-constexpr int kPackedSlots = 2048;
+// segment only.  As for Staged, a row longer than kPackedSlots (or a copy past
+// 32-bit slot indices) leaves the copy empty with ok false.  Built by
+// packed_layout (layouts.h).
 struct Packed {
   bool ok = true;
   Sell data;  // col, src, val, val32, slots (off / row0 / rowlen unused)

@@ -307,162 +307,40 @@ void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col
   S.val32.alloc(std::max<int64_t>(1, slots));
 }
 
-// Block partition of each level of a sweep over the CSR pattern (ptr) for the
-// staged kernels (Staged in gbs_internal.h).  A level gets about
-// max(ceil(entries / kStagedEntries), ceil(rows / kStagedRows)) blocks,
-// raised to the SM count (or to a multiple of it), and rows are cut greedily
-// at equal shares of entries + 4 per row; a block never exceeds the caps.
+// Upload of the staged partition of one sweep (layouts.h); an unavailable
+// layout (a row longer than a block) stays empty with ok false.
 void build_staged(const std::vector<int32_t>& ptr, const std::vector<int32_t>& lev_ptr, int n_sm,
                   Staged& T, cudaStream_t stream) {
-  const int nlev = (int)lev_ptr.size() - 1;
-  std::vector<int32_t> brow, desc;
-  T.lev_b.assign(nlev, 0);
-  T.lev_nb.assign(nlev, 0);
-  T.lev_ecap.assign(nlev, 0);
-  T.lev_rcap.assign(nlev, 0);
-  T.lev_mean.assign(nlev, 0.f);
-  T.ecap = T.rcap = 0;
-  T.ok = true;
-  for (int32_t r = lev_ptr[0]; r < lev_ptr[nlev]; ++r)
-    if (ptr[r + 1] - ptr[r] > kStagedEntries) T.ok = false;
-  if (!T.ok) return;
-  for (int l = 0; l < nlev; ++l) {
-    const int32_t r0 = lev_ptr[l], r1 = lev_ptr[l + 1];
-    const int64_t R = r1 - r0, E = (int64_t)ptr[r1] - ptr[r0];
-    int64_t nb = std::max<int64_t>((E + kStagedEntries - 1) / kStagedEntries, (R + kStagedRows - 1) / kStagedRows);
-    nb = nb <= n_sm ? std::min<int64_t>(R, n_sm) : (nb + n_sm - 1) / n_sm * n_sm;
-    const double share = (double)(E + 4 * R) / (double)std::max<int64_t>(1, nb);
-    T.lev_b[l] = (int32_t)(desc.size() / 4);
-    T.lev_mean[l] = R ? (float)((double)E / (double)R) : 0.f;
-    brow.assign(1, r0);
-    int64_t acc = 0, ent = 0, rows = 0, cuts = 0;
-    for (int32_t r = r0; r < r1; ++r) {
-      const int64_t len = ptr[r + 1] - ptr[r];
-      if (len > kStagedEntries) fail(GB_ERR_INVALID_ARG, "row too long for the staged sweep");
-      const bool full = ent + len > kStagedEntries || rows == kStagedRows;
-      const bool due = rows > 0 && (double)(acc + len + 4) > share * (double)(cuts + 1);
-      if (rows > 0 && (full || due)) {
-        brow.push_back(r);
-        T.lev_ecap[l] = std::max<int32_t>(T.lev_ecap[l], (int32_t)ent);
-        T.lev_rcap[l] = std::max<int32_t>(T.lev_rcap[l], (int32_t)rows);
-        ++cuts;
-        ent = rows = 0;
-      }
-      acc += len + 4;
-      ent += len;
-      ++rows;
-    }
-    brow.push_back(r1);
-    T.lev_ecap[l] = std::max<int32_t>(T.lev_ecap[l], (int32_t)ent);
-    T.lev_rcap[l] = std::max<int32_t>(T.lev_rcap[l], (int32_t)rows);
-    T.lev_nb[l] = (int32_t)(cuts + 1);
-    T.ecap = std::max(T.ecap, T.lev_ecap[l]);
-    T.rcap = std::max(T.rcap, T.lev_rcap[l]);
-    for (size_t b = 0; b + 1 < brow.size(); ++b) {
-      desc.push_back(brow[b]);
-      desc.push_back(brow[b + 1]);
-      desc.push_back(ptr[brow[b]]);
-      desc.push_back(ptr[brow[b + 1]]);
-    }
-  }
-  T.desc.upload(desc.data(), desc.size(), stream);
+  StagedLayout h = staged_layout(ptr, lev_ptr, n_sm);
+  T.ok = h.ok;
+  T.lev_b = std::move(h.lev_b);
+  T.lev_nb = std::move(h.lev_nb);
+  T.lev_ecap = std::move(h.lev_ecap);
+  T.lev_rcap = std::move(h.lev_rcap);
+  T.lev_mean = std::move(h.lev_mean);
+  T.ecap = h.ecap;
+  T.rcap = h.rcap;
+  if (T.ok) T.desc.upload(h.desc.data(), h.desc.size(), stream);
 }
 
-// Packed k-major copy of each level of a sweep over the CSR pattern (ptr,
-// col) for the packed kernels (Packed in gbs_internal.h).  Blocks are cut as
-// in build_staged, with the padded size rows * (longest row) as the cap.
-// With split = +1 (forward sweep) or -1 (backward sweep) every row's entries
-// are divided by the level of their column: the entries of the level the
-// sweep finished just before (l - split) form a second k-major segment after
-// the others, and a block's padded size is rows * (longest first part +
-// longest second part).  desc.w then holds lo + (lr << 16).
+// Upload of the packed copy of one sweep (layouts.h; split 0, +1 forward or
+// -1 backward); values are filled from the factor after factorisation.
 void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
                   const std::vector<int32_t>& lev_ptr, int n_sm, Packed& T, cudaStream_t stream,
                   int split = 0) {
-  const int nlev = (int)lev_ptr.size() - 1;
-  std::vector<int32_t> desc, pcol, psrc;
-  std::vector<int32_t> lev_of;
-  if (split) {
-    lev_of.assign(lev_ptr[nlev], 0);
-    for (int l = 0; l < nlev; ++l)
-      for (int32_t r = lev_ptr[l]; r < lev_ptr[l + 1]; ++r) lev_of[r] = l;
-  }
-  T.lev_b.assign(nlev, 0);
-  T.lev_nb.assign(nlev, 0);
-  T.lev_mean.assign(nlev, 0.f);
-  T.cap = T.rcap = 0;
-  T.ok = true;
-  for (int32_t r = lev_ptr[0]; r < lev_ptr[nlev]; ++r)
-    if (ptr[r + 1] - ptr[r] > kPackedSlots) T.ok = false;
+  PackedLayout h = packed_layout(ptr, col, lev_ptr, n_sm, split);
+  T.ok = h.ok;
+  T.lev_b = std::move(h.lev_b);
+  T.lev_nb = std::move(h.lev_nb);
+  T.lev_mean = std::move(h.lev_mean);
+  T.cap = h.cap;
+  T.rcap = h.rcap;
   if (!T.ok) return;
-  // entries of row r in the second segment (0 without a split)
-  auto recent = [&](int32_t r, int l) {
-    if (!split) return 0;
-    int32_t m = 0;
-    for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) m += lev_of[col[e]] == l - split;
-    return (int)m;
-  };
-  auto emit = [&](int l, int32_t rb, int32_t nr, int32_t lo, int32_t lr) {
-    const int64_t off = (int64_t)pcol.size();
-    const int64_t len = (int64_t)lo + lr;
-    if (off + (int64_t)nr * len >= INT32_MAX) fail(GB_ERR_INVALID_ARG, "packed copy exceeds 32-bit indexing");
-    desc.push_back(rb);
-    desc.push_back(nr);
-    desc.push_back((int32_t)off);
-    desc.push_back(lo + (lr << 16));
-    pcol.resize(off + (int64_t)nr * len, -1);
-    psrc.resize(off + (int64_t)nr * len, -1);
-    for (int32_t i = 0; i < nr; ++i) {
-      int32_t ko = 0, kr = 0;
-      for (int32_t e = ptr[rb + i]; e < ptr[rb + i + 1]; ++e) {
-        const bool second = split && lev_of[col[e]] == l - split;
-        const int64_t slot = second ? off + (int64_t)nr * lo + (int64_t)(kr++) * nr + i
-                                    : off + (int64_t)(ko++) * nr + i;
-        pcol[slot] = col[e];
-        psrc[slot] = e;
-      }
-    }
-    T.cap = std::max<int>(T.cap, (int)(nr * len));
-    T.rcap = std::max(T.rcap, nr);
-  };
-  for (int l = 0; l < nlev; ++l) {
-    const int32_t r0 = lev_ptr[l], r1 = lev_ptr[l + 1];
-    const int64_t R = r1 - r0, E = (int64_t)ptr[r1] - ptr[r0];
-    int64_t nb = std::max<int64_t>((E + kPackedSlots - 1) / kPackedSlots, (R + kStagedRows - 1) / kStagedRows);
-    nb = nb <= n_sm ? std::min<int64_t>(R, n_sm) : (nb + n_sm - 1) / n_sm * n_sm;
-    const double share = (double)(E + 4 * R) / (double)std::max<int64_t>(1, nb);
-    T.lev_b[l] = (int32_t)(desc.size() / 4);
-    int64_t first = 0;  // entries of the level in the first segment
-    int32_t rb = r0, rows = 0, lo = 0, lr = 0, cuts = 0;
-    int64_t acc = 0;
-    for (int32_t r = r0; r < r1; ++r) {
-      const int32_t len = ptr[r + 1] - ptr[r];
-      const int32_t m = recent(r, l);
-      first += len - m;
-      if (len > kPackedSlots) fail(GB_ERR_INVALID_ARG, "row too long for the packed sweep");
-      const bool full =
-          (int64_t)(rows + 1) * (std::max(lo, len - m) + std::max(lr, m)) > kPackedSlots || rows == kStagedRows;
-      const bool due = rows > 0 && (double)(acc + len + 4) > share * (double)(cuts + 1);
-      if (rows > 0 && (full || due)) {
-        emit(l, rb, rows, lo, lr);
-        ++cuts;
-        rb = r;
-        rows = lo = lr = 0;
-      }
-      acc += len + 4;
-      lo = std::max(lo, len - m);
-      lr = std::max(lr, m);
-      ++rows;
-    }
-    emit(l, rb, rows, lo, lr);
-    T.lev_nb[l] = cuts + 1;
-    T.lev_mean[l] = R ? (float)((double)first / (double)R) : 0.f;
-  }
-  T.desc.upload(desc.data(), desc.size(), stream);
+  T.desc.upload(h.desc.data(), h.desc.size(), stream);
   Sell& S = T.data;
-  S.slots = (int64_t)pcol.size();
-  S.col.upload(pcol.data(), std::max<size_t>(1, pcol.size()), stream);
-  S.src.upload(psrc.data(), std::max<size_t>(1, psrc.size()), stream);
+  S.slots = (int64_t)h.col.size();
+  S.col.upload(h.col.data(), std::max<size_t>(1, h.col.size()), stream);
+  S.src.upload(h.src.data(), std::max<size_t>(1, h.src.size()), stream);
   S.val.alloc(std::max<int64_t>(1, S.slots));
   S.val32.alloc(std::max<int64_t>(1, S.slots));
 }
