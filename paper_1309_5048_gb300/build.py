@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbstokes.so")
-SOURCES = ["setup.cpp", "layouts.cpp", "assemble.cu", "factor.cu", "solver.cu", "capi.cpp"]
-HEADERS = ["gbs_internal.h", "gbs_device.cuh", "solver_kernels.cuh", "layouts.h"]
+SOURCES = ["setup.cpp", "pattern.cpp", "layouts.cpp", "assemble.cu", "factor.cu", "solver.cu", "capi.cpp"]
+HEADERS = ["gbs_internal.h", "gbs_device.cuh", "solver_kernels.cuh", "layouts.h", "pattern.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

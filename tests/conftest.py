@@ -20,6 +20,21 @@ def oracle_mod():
     return oracle
 
 
+@pytest.fixture(scope="session")
+def host_lib(tmp_path_factory):
+    """The library's CUDA-free host builders (csrc/pattern.cpp and
+    csrc/layouts.cpp) with the test entry points of tests/layout_shim.cpp,
+    compiled by g++ into a shared library."""
+    import ctypes
+    import subprocess
+    csrc = os.path.join(ROOT, "paper_1309_5048_gb300", "csrc")
+    out = tmp_path_factory.mktemp("hostlib") / "libhost.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I", csrc,
+                    os.path.join(ROOT, "tests", "layout_shim.cpp"), os.path.join(csrc, "layouts.cpp"),
+                    os.path.join(csrc, "pattern.cpp"), "-o", str(out)], check=True)
+    return ctypes.CDLL(str(out))
+
+
 def read_golden(name):
     rows = []
     with open(os.path.join(ROOT, "tests", "golden", name)) as fh:

@@ -1,14 +1,18 @@
-// Test-only C entry points around the host layout builders (layouts.h), so
-// that the CPU tests can check the staged and packed layouts of the IC(0)
-// sweeps without a GPU.  Compiled by tests/test_layouts.py with g++.
+// Test-only C entry points around the host builders of the library: the
+// sparsity patterns, ordering and level sets (pattern.h) and the staged and
+// packed layouts of the IC(0) sweeps (layouts.h), so that the CPU tests can
+// check them without a GPU.  Compiled by tests/test_layouts.py and
+// tests/test_pattern.py with g++.
 #include <cstring>
 #include <vector>
 
 #include "layouts.h"
+#include "pattern.h"
 
 namespace {
 gbs::StagedLayout g_staged;
 gbs::PackedLayout g_packed;
+gbs::HostPattern g_pattern;
 
 std::vector<int32_t> copy(const int32_t* p, int64_t n) { return std::vector<int32_t>(p, p + n); }
 }  // namespace
@@ -51,5 +55,36 @@ void lt_packed_fetch(int32_t* desc, int32_t* col, int32_t* src, int32_t* lev_b, 
   std::memcpy(lev_mean, g_packed.lev_mean.data(), g_packed.lev_mean.size() * 4);
   caps[0] = g_packed.cap;
   caps[1] = g_packed.rcap;
+}
+
+// Builds the pattern; returns 0, or 1 with the message in msg (size cap).
+int lt_pattern(int32_t dim, int32_t N, int32_t p, int32_t ordering, int64_t* sizes, char* msg, int32_t cap) {
+  try {
+    g_pattern = gbs::build_pattern(dim, N, p, ordering);
+  } catch (const gbs::PatternError& e) {
+    std::strncpy(msg, e.what(), cap - 1);
+    msg[cap - 1] = 0;
+    return 1;
+  }
+  const gbs::HostPattern& P = g_pattern;
+  const int64_t v[] = {P.n_u, P.n_p, P.nlev, P.nrlev, P.ncolours, P.nnzA, P.nnzL, P.nnzB, P.nnzQ,
+                       (int64_t)P.L_col.size(), (int64_t)P.U_col.size()};
+  std::memcpy(sizes, v, sizeof(v));
+  return 0;
+}
+
+// Copies one array of the last pattern: 0 perm, 1 level, 2 rlevel, 3 lev_ptr,
+// 4 int_to_pos, 5 order, 6 iorder, 7 A ptr, 8 A col, 9 A diag, 10 L ptr,
+// 11 L col, 12 U ptr, 13 U col, 14 U map, 15 B ptr, 16 B col, 17 Bt ptr,
+// 18 Bt col, 19 Bt map, 20 Q ptr, 21 Q col.  Returns its length.
+int64_t lt_pattern_array(int32_t which, int32_t* out) {
+  const gbs::HostPattern& P = g_pattern;
+  const std::vector<int32_t>* a[] = {&P.perm,   &P.level,  &P.rlevel, &P.lev_ptr, &P.int_to_pos, &P.order,
+                                     &P.iorder, &P.hA_ptr, &P.hA_col, &P.A_diag,  &P.L_ptr,      &P.L_col,
+                                     &P.U_ptr,  &P.U_col,  &P.U_map,  &P.hB_ptr,  &P.hB_col,     &P.Bt_ptr,
+                                     &P.Bt_col, &P.Bt_map, &P.Q_ptr,  &P.Q_col};
+  if (which < 0 || which >= (int32_t)(sizeof(a) / sizeof(a[0]))) return -1;
+  if (out) std::memcpy(out, a[which]->data(), a[which]->size() * 4);
+  return (int64_t)a[which]->size();
 }
 }
