@@ -1,5 +1,6 @@
-// layouts.cpp -- host construction of the staged and packed block layouts of
-// the IC(0) sweeps (layouts.h).  No CUDA: setup uploads the results.
+// layouts.cpp -- host construction of the SELL-32 copies and of the staged
+// and packed block layouts of the IC(0) sweeps (layouts.h).  No CUDA: setup
+// uploads the results.
 #include "layouts.h"
 
 #include <algorithm>
@@ -24,6 +25,45 @@ bool rows_fit(const std::vector<int32_t>& ptr, const std::vector<int32_t>& lev_p
 }
 
 }  // namespace
+
+SellLayout sell_layout(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
+                       const std::vector<int32_t>& lev_ptr) {
+  SellLayout S;
+  const int nlev = (int)lev_ptr.size() - 1;
+  S.lev_slice.assign(nlev + 1, 0);
+  int64_t slots = 0;
+  for (int l = 0; l < nlev; ++l) {
+    S.lev_slice[l] = (int32_t)S.row0.size();
+    for (int32_t r = lev_ptr[l]; r < lev_ptr[l + 1]; r += 32) {
+      const int32_t r1 = std::min(r + 32, lev_ptr[l + 1]);
+      int32_t len = 0;
+      for (int32_t q = r; q < r1; ++q) len = std::max(len, ptr[q + 1] - ptr[q]);
+      S.row0.push_back(r);
+      S.off.push_back((int32_t)std::min<int64_t>(slots, INT_MAX));
+      slots += (int64_t)32 * len;
+    }
+  }
+  S.lev_slice[nlev] = (int32_t)S.row0.size();
+  if (slots >= INT_MAX) return SellLayout{false};
+  S.nslices = (int)S.row0.size();
+  S.row0.push_back(lev_ptr[nlev]);
+  S.off.push_back((int32_t)slots);
+  S.slots = slots;
+  S.rowlen.assign(ptr.size() - 1, 0);
+  S.col.assign(slots, 0);
+  S.src.assign(slots, -1);
+  for (int s = 0; s < S.nslices; ++s)
+    for (int32_t q = S.row0[s]; q < S.row0[s + 1]; ++q) {
+      const int lane = q - S.row0[s];
+      S.rowlen[q] = ptr[q + 1] - ptr[q];
+      for (int32_t k = 0; k < S.rowlen[q]; ++k) {
+        const int64_t slot = S.off[s] + (int64_t)32 * k + lane;
+        S.col[slot] = col[ptr[q] + k];
+        S.src[slot] = ptr[q] + k;
+      }
+    }
+  return S;
+}
 
 StagedLayout staged_layout(const std::vector<int32_t>& ptr, const std::vector<int32_t>& lev_ptr, int n_sm) {
   StagedLayout T;

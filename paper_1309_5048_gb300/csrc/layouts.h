@@ -1,7 +1,8 @@
-// layouts.h -- host construction of the block layouts of the IC(0) sweeps
-// (Sec. 6.4, "PCG(A)": the forward and backward triangular solves of the
-// IC(0) preconditioner, one launch per level of the factor's DAG).  Plain
-// C++ without CUDA: setup uploads what these functions return.
+// layouts.h -- host construction of the kernel layouts of the sparse
+// operators: SELL-32 copies (inner SpMV and sweeps) and the block layouts of
+// the IC(0) sweeps (Sec. 6.4, "PCG(A)": the forward and backward triangular
+// solves of the IC(0) preconditioner, one launch per level of the factor's
+// DAG).  Plain C++ without CUDA: setup uploads what these functions return.
 //
 // Input: a triangular factor as CSR over the internal numbering (rows sorted
 // by level, so level l is the row range [lev_ptr[l], lev_ptr[l+1])), strict
@@ -19,6 +20,22 @@ namespace gbs {
 constexpr int kStagedRows = 256;
 constexpr int kStagedEntries = 2048;
 constexpr int kPackedSlots = 2048;
+
+// SELL-32 copy: rows cut into slices of 32 consecutive rows that never cross
+// a level; slice s starts at row row0[s] (row0[nslices] = end) and slot
+// off[s] (off[nslices] = slots); entry k of the row in lane i sits at
+// off[s] + 32 k + i, with col the column and src its CSR position (padding
+// past rowlen: col 0, src -1, never read).  Level l owns slices
+// [lev_slice[l], lev_slice[l+1]).  ok is false (the rest empty) when the copy
+// would exceed 32-bit slot indices.
+struct SellLayout {
+  bool ok = true;
+  int nslices = 0;
+  int64_t slots = 0;
+  std::vector<int32_t> row0, off, rowlen, col, src, lev_slice;
+};
+SellLayout sell_layout(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
+                       const std::vector<int32_t>& lev_ptr);
 
 // Staged partition: block b is desc[4b .. 4b+3] = {first row, end row, first
 // entry, end entry} (CSR positions); level l owns blocks lev_b[l] ..

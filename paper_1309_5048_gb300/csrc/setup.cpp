@@ -12,50 +12,23 @@ namespace gbs {
 
 namespace {
 
-// SELL-32 copy of a CSR pattern (rows in internal numbering) with slices of
-// 32 rows that never cross a level boundary (lev_ptr).
+// Upload of the SELL-32 copy of a CSR pattern (layouts.h); lev_slice
+// receives the slice range of every level.
 void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col,
                 const std::vector<int32_t>& lev_ptr, std::vector<int32_t>& lev_slice, Sell& S,
                 cudaStream_t stream) {
-  const int nlev = (int)lev_ptr.size() - 1;
-  std::vector<int32_t> row0, off, rowlen(ptr.size() - 1);
-  lev_slice.assign(nlev + 1, 0);
-  int64_t slots = 0;
-  for (int l = 0; l < nlev; ++l) {
-    lev_slice[l] = (int32_t)row0.size();
-    for (int32_t r = lev_ptr[l]; r < lev_ptr[l + 1]; r += 32) {
-      const int32_t r1 = std::min(r + 32, lev_ptr[l + 1]);
-      int32_t len = 0;
-      for (int32_t q = r; q < r1; ++q) len = std::max(len, ptr[q + 1] - ptr[q]);
-      row0.push_back(r);
-      off.push_back((int32_t)slots);
-      slots += (int64_t)32 * len;
-    }
-  }
-  lev_slice[nlev] = (int32_t)row0.size();
-  if (slots >= INT32_MAX) fail(GB_ERR_INVALID_ARG, "SELL copy exceeds 32-bit indexing");
-  S.nslices = (int)row0.size();
-  row0.push_back(lev_ptr[nlev]);
-  off.push_back((int32_t)slots);
-  std::vector<int32_t> scol(slots, 0), ssrc(slots, -1);
-  for (int s = 0; s < S.nslices; ++s)
-    for (int32_t q = row0[s]; q < row0[s + 1]; ++q) {
-      const int lane = q - row0[s];
-      rowlen[q] = ptr[q + 1] - ptr[q];
-      for (int32_t k = 0; k < rowlen[q]; ++k) {
-        const int64_t slot = off[s] + (int64_t)32 * k + lane;
-        scol[slot] = col[ptr[q] + k];
-        ssrc[slot] = ptr[q] + k;
-      }
-    }
-  S.slots = slots;
-  S.row0.upload(row0.data(), row0.size(), stream);
-  S.off.upload(off.data(), off.size(), stream);
-  S.rowlen.upload(rowlen.data(), rowlen.size(), stream);
-  S.col.upload(scol.data(), std::max<size_t>(1, scol.size()), stream);
-  S.src.upload(ssrc.data(), std::max<size_t>(1, ssrc.size()), stream);
-  S.val.alloc(std::max<int64_t>(1, slots));
-  S.val32.alloc(std::max<int64_t>(1, slots));
+  SellLayout h = sell_layout(ptr, col, lev_ptr);
+  if (!h.ok) fail(GB_ERR_INVALID_ARG, "SELL copy exceeds 32-bit indexing");
+  lev_slice = std::move(h.lev_slice);
+  S.nslices = h.nslices;
+  S.slots = h.slots;
+  S.row0.upload(h.row0.data(), h.row0.size(), stream);
+  S.off.upload(h.off.data(), h.off.size(), stream);
+  S.rowlen.upload(h.rowlen.data(), h.rowlen.size(), stream);
+  S.col.upload(h.col.data(), std::max<size_t>(1, h.col.size()), stream);
+  S.src.upload(h.src.data(), std::max<size_t>(1, h.src.size()), stream);
+  S.val.alloc(std::max<int64_t>(1, h.slots));
+  S.val32.alloc(std::max<int64_t>(1, h.slots));
 }
 
 // Upload of the staged partition of one sweep (layouts.h); an unavailable

@@ -1,6 +1,7 @@
 // Test-only C entry points around the host builders of the library: the
-// sparsity patterns, ordering and level sets (pattern.h) and the staged and
-// packed layouts of the IC(0) sweeps (layouts.h), so that the CPU tests can
+// sparsity patterns, ordering and level sets (pattern.h), the SELL-32 copies
+// and the staged and packed layouts of the IC(0) sweeps (layouts.h), so that
+// the CPU tests can
 // check them without a GPU.  Compiled by tests/test_layouts.py and
 // tests/test_pattern.py with g++.
 #include <cstring>
@@ -13,11 +14,31 @@ namespace {
 gbs::StagedLayout g_staged;
 gbs::PackedLayout g_packed;
 gbs::HostPattern g_pattern;
+gbs::SellLayout g_sell;
 
 std::vector<int32_t> copy(const int32_t* p, int64_t n) { return std::vector<int32_t>(p, p + n); }
 }  // namespace
 
 extern "C" {
+
+// SELL-32 copy; sizes[0..2] = ok, slices, slots.
+void lt_sell(const int32_t* ptr, const int32_t* col, int32_t n, const int32_t* lev_ptr, int32_t nlev,
+             int64_t* sizes) {
+  std::vector<int32_t> p = copy(ptr, n + 1);
+  g_sell = gbs::sell_layout(p, copy(col, p[n]), copy(lev_ptr, nlev + 1));
+  sizes[0] = g_sell.ok;
+  sizes[1] = g_sell.nslices;
+  sizes[2] = g_sell.slots;
+}
+
+void lt_sell_fetch(int32_t* row0, int32_t* off, int32_t* rowlen, int32_t* col, int32_t* src, int32_t* lev_slice) {
+  std::memcpy(row0, g_sell.row0.data(), g_sell.row0.size() * 4);
+  std::memcpy(off, g_sell.off.data(), g_sell.off.size() * 4);
+  std::memcpy(rowlen, g_sell.rowlen.data(), g_sell.rowlen.size() * 4);
+  std::memcpy(col, g_sell.col.data(), g_sell.col.size() * 4);
+  std::memcpy(src, g_sell.src.data(), g_sell.src.size() * 4);
+  std::memcpy(lev_slice, g_sell.lev_slice.data(), g_sell.lev_slice.size() * 4);
+}
 
 // Builds the layout; sizes[0..2] = ok, blocks, slots (slots: packed only).
 void lt_staged(const int32_t* ptr, int32_t n, const int32_t* lev_ptr, int32_t nlev, int32_t n_sm,

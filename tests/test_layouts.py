@@ -1,5 +1,5 @@
-"""The block layouts of the IC(0) sweeps, built on the host (layouts.h), on
-the CPU: bit-exact index work, checked entry by entry.
+"""The SELL-32 copies and the block layouts of the IC(0) sweeps, built on the
+host (layouts.h), on the CPU: bit-exact index work, checked entry by entry.
 
 The factor patterns are the library's: IC(0) keeps the pattern of the strict
 lower part of the reordered A_h (Sec. 6.4), the levels are the longest-path
@@ -214,3 +214,43 @@ def test_rows_longer_than_a_block_make_the_layouts_unavailable(lt, extra, ok):
         if ok:
             check_packed(lay, ptr, col, lev_ptr, 152, split)
     assert (staged(lt, ptr, lev_ptr, 152) is not None) == ok
+
+
+def sell(lt, ptr, col, lev_ptr):
+    n, nlev = len(ptr) - 1, len(lev_ptr) - 1
+    sizes = np.zeros(3, np.int64)
+    lt.lt_sell(_p(ptr), _p(col), C.c_int32(n), _p(lev_ptr), C.c_int32(nlev), _p(sizes))
+    ok, ns, slots = (int(v) for v in sizes)
+    assert ok
+    row0 = np.zeros(ns + 1, np.int32)
+    off = np.zeros(ns + 1, np.int32)
+    rowlen = np.zeros(max(n, 1), np.int32)
+    scol = np.zeros(max(slots, 1), np.int32)
+    ssrc = np.zeros(max(slots, 1), np.int32)
+    lev_slice = np.zeros(nlev + 1, np.int32)
+    lt.lt_sell_fetch(_p(row0), _p(off), _p(rowlen), _p(scol), _p(ssrc), _p(lev_slice))
+    return row0, off, rowlen[:n], scol[:slots], ssrc[:slots], lev_slice
+
+
+@pytest.mark.parametrize("dim,N,p,ordering", CASES)
+def test_sell_copies(oracle_mod, lt, dim, N, p, ordering):
+    """Slices of at most 32 rows inside one level, each padded to its longest
+    row; entry k of the row in lane i at off[s] + 32 k + i, every entry once,
+    padding marked -1 in the slot map."""
+    Lptr, Lcol, Uptr, Ucol, lev_ptr = factor_patterns(oracle_mod, dim, N, p, ordering)
+    for ptr, col in ((Lptr, Lcol), (Uptr, Ucol)):
+        row0, off, rowlen, scol, ssrc, lev_slice = sell(lt, ptr, col, lev_ptr)
+        n, ns = len(ptr) - 1, len(row0) - 1
+        assert np.array_equal(rowlen, np.diff(ptr))
+        assert row0[0] == 0 and row0[-1] == n and np.all(np.diff(row0) >= 1) and np.all(np.diff(row0) <= 32)
+        for l in range(len(lev_ptr) - 1):  # the slices of a level tile exactly its rows
+            assert row0[lev_slice[l]] == lev_ptr[l] and row0[lev_slice[l + 1]] == lev_ptr[l + 1]
+        expect = np.full(len(ssrc), -1, np.int64)
+        for s in range(ns):
+            rows = np.arange(row0[s], row0[s + 1])
+            assert off[s + 1] - off[s] == 32 * rowlen[rows].max(initial=0)
+            for i, r in enumerate(rows):
+                expect[off[s] + 32 * np.arange(rowlen[r]) + i] = np.arange(ptr[r], ptr[r + 1])
+        assert np.array_equal(expect, ssrc)
+        real = ssrc >= 0
+        assert np.array_equal(scol[real], col[ssrc[real]])
