@@ -79,6 +79,10 @@ int guarded(F fn) {
 }
 
 void set_error(const char* msg) { g_last_error = msg; }
+int bad_arg(const char* msg) {
+  set_error(msg);
+  return GB_ERR_INVALID_ARG;
+}
 
 // Orders the context's work stream after the caller's stream on entry and
 // the caller's stream after the work stream on exit.
@@ -152,7 +156,7 @@ int gb_sizes(const gb_ctx* h, int64_t* out) {
 }
 
 int gb_assemble(gb_ctx* h, double nu, double cpen) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     assemble(h->c, nu, cpen);
@@ -160,7 +164,7 @@ int gb_assemble(gb_ctx* h, double nu, double cpen) {
 }
 
 int gb_load_fourier(gb_ctx* h, int nmodes, const int32_t* kappa_host, const double* amp_host, double* f_dev) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     load_fourier(h->c, nmodes, kappa_host, amp_host, f_dev);
@@ -168,7 +172,7 @@ int gb_load_fourier(gb_ctx* h, int nmodes, const int32_t* kappa_host, const doub
 }
 
 int gb_load_manufactured(gb_ctx* h, double* f_dev) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     load_manufactured(h->c, f_dev);
@@ -176,7 +180,7 @@ int gb_load_manufactured(gb_ctx* h, double* f_dev) {
 }
 
 int gb_load_cavity(gb_ctx* h, double* f_dev) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     load_cavity(h->c, f_dev);
@@ -184,7 +188,7 @@ int gb_load_cavity(gb_ctx* h, double* f_dev) {
 }
 
 int gb_factor_ic0(gb_ctx* h, int64_t* breakdown_row_host) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   int64_t row = -1;
   int st = guarded([&] {
     StreamOrder order(h->c);
@@ -209,7 +213,7 @@ static int solve_result(int st) {
 
 int gb_solve(gb_ctx* h, const double* rhs_dev, double* x_dev, int k, const gb_solve_opts* opts,
              gb_info* info_host) {
-  if (!h || !opts) return GB_ERR_INVALID_ARG;
+  if (!h || !opts) return bad_arg("null context or options");
   int st2 = GB_OK;
   int st = guarded([&] {
     StreamOrder order(h->c);
@@ -220,7 +224,7 @@ int gb_solve(gb_ctx* h, const double* rhs_dev, double* x_dev, int k, const gb_so
 
 int gb_solve_host(gb_ctx* h, const double* rhs_host, double* x_host, int k, const gb_solve_opts* opts,
                   gb_info* info_host) {
-  if (!h || !opts) return GB_ERR_INVALID_ARG;
+  if (!h || !opts) return bad_arg("null context or options");
   int st2 = GB_OK;
   int st = guarded([&] {
     StreamOrder order(h->c);
@@ -231,7 +235,7 @@ int gb_solve_host(gb_ctx* h, const double* rhs_host, double* x_host, int k, cons
 
 int gb_solve_adjoint(gb_ctx* h, const double* grad_dev, double* lam_dev, int k, const gb_solve_opts* opts,
                      gb_info* info_host) {
-  if (!h || !opts) return GB_ERR_INVALID_ARG;
+  if (!h || !opts) return bad_arg("null context or options");
   int st2 = GB_OK;
   int st = guarded([&] {
     StreamOrder order(h->c);
@@ -241,7 +245,7 @@ int gb_solve_adjoint(gb_ctx* h, const double* grad_dev, double* lam_dev, int k, 
 }
 
 int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double* out_host) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     dnu(h->c, lam_dev, x_dev, k, out_host);
@@ -293,7 +297,7 @@ int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv)
 }
 
 int gb_lanczos(gb_ctx* h, int rhs, double* delta_host, double* gamma_host, int cap, int* count) {
-  if (!h || !count) return GB_ERR_INVALID_ARG;
+  if (!h || !count) return bad_arg("null context or count");
   return guarded([&] {
     StreamOrder order(h->c);
     *count = lanczos_coeffs(h->c, rhs, delta_host, gamma_host, cap);
@@ -301,7 +305,7 @@ int gb_lanczos(gb_ctx* h, int rhs, double* delta_host, double* gamma_host, int c
 }
 
 int gb_ritz_extremes(gb_ctx* h, int rhs, int exclude_one, double* out_host) {
-  if (!h || !out_host) return GB_ERR_INVALID_ARG;
+  if (!h || !out_host) return bad_arg("null context or output");
   return guarded([&] {
     StreamOrder order(h->c);
     ritz_extremes(h->c, rhs, exclude_one, out_host);
@@ -309,7 +313,7 @@ int gb_ritz_extremes(gb_ctx* h, int rhs, int exclude_one, double* out_host) {
 }
 
 int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
-  if (!h || !ms_host) return GB_ERR_INVALID_ARG;
+  if (!h || !ms_host) return bad_arg("null context or output");
   return guarded([&] {
     StreamOrder order(h->c);
     *ms_host = time_kernel(h->c, which, reps);
@@ -317,7 +321,7 @@ int gb_time_kernel(gb_ctx* h, int which, int reps, double* ms_host) {
 }
 
 int gb_dnu_noalloc(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double* out_host) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     dnu_noalloc(h->c, lam_dev, x_dev, k, out_host);
@@ -325,7 +329,7 @@ int gb_dnu_noalloc(gb_ctx* h, const double* lam_dev, const double* x_dev, int k,
 }
 
 int gb_apply(gb_ctx* h, int which, const double* x_dev, double* y_dev) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     StreamOrder order(h->c);
     apply_operator(h->c, which, x_dev, y_dev);
@@ -333,7 +337,7 @@ int gb_apply(gb_ctx* h, int which, const double* x_dev, double* y_dev) {
 }
 
 int gb_export(gb_ctx* h, int what, void* p0, void* p1, void* p2) {
-  if (!h) return GB_ERR_INVALID_ARG;
+  if (!h) return bad_arg("null context");
   return guarded([&] {
     Ctx& c = h->c;
     StreamOrder order(c);

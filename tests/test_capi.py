@@ -84,3 +84,21 @@ int main(void) {
     assert offs == [gb.gb_info.inner_its_total.offset, gb.gb_info.inner_its_max.offset,
                     gb.gb_info.relres_true.offset, gb.gb_info.q_inner_its_total.offset,
                     gb.gb_info.q_inner_its_max.offset, gb.gb_info.status.offset]
+
+
+def test_every_entry_point_rejects_a_null_context(lib):
+    """Every call returns GB_ERR_INVALID_ARG (1) with a message for a null
+    context before any device work, so this runs without a GPU; gb_destroy
+    accepts a null context."""
+    import paper_1309_5048_gb300 as gb
+    L = gb.load_library()
+    for name in gb.EXPORTED:
+        if name in ("gb_status_string", "gb_last_error", "gb_destroy"):
+            continue
+        f = getattr(L, name)
+        args = [1.0 if t is C.c_double else (1 if t in (C.c_int, C.c_int64) else None) for t in f.argtypes]
+        assert f(*args) == 1, name
+        assert L.gb_last_error(), name
+    L.gb_destroy(None)
+    codes = [L.gb_status_string(k) for k in range(8)]
+    assert len(set(codes)) == 8 and all(codes)
