@@ -228,18 +228,22 @@ int gb_solve_adjoint(gb_ctx* ctx, const double* grad_dev, double* lam_dev, int k
 int gb_dnu(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
 
 /* The same dL/dnu as gb_dnu, computed without allocating any device memory.
- * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- code running while a CUDA graph is being
- * captured, programs whose device memory belongs to a pool or framework that
- * forbids further allocations, callers with an exhausted memory budget.
- * (gb_dnu may allocate the context's workspace on first use.)  The reduction
- * scratch is a static device array inside the library, sized for k <= 32 and
- * the largest launch (about 304 KiB); every GPU that loads the library holds
- * it until the process exits.  k > 32 is rejected with GB_ERR_INVALID_ARG.
- * The first call on a device looks up that array's device address (make it
- * before any stream capture).  All calls share the array, so calls that
- * overlap on the GPU race; the context must be assembled.  Arguments, layout
- * and result are those of gb_dnu. */
+ * The paper has no counterpart.  It is meant for callers that cannot call
+ * cudaMalloc when they need the viscosity gradient: programs whose device
+ * memory is handed out by their own pool or framework, which forbids raw
+ * allocations next to it (they would fragment the pool or exceed its
+ * budget), and callers that have already spent a fixed memory budget.
+ * gb_dnu may allocate the context's solve workspace on first use; this call
+ * never does.  Its reduction scratch is a static device array inside the
+ * library, sized for k <= 32 and the largest launch (about 304 KiB); every
+ * GPU that loads the library holds it until the process exits.  k > 32 is
+ * rejected with GB_ERR_INVALID_ARG.  The first call on a device looks up
+ * that array's device address (make it before any stream capture).  All
+ * calls share the array, so calls that overlap on the GPU race; each call
+ * clears the parts that must start at zero.  The call copies the k results
+ * to out_host and waits for them on the context's stream before it
+ * returns.  The context must be assembled.  Arguments, layout and result are
+ * those of gb_dnu. */
 int gb_dnu_noalloc(gb_ctx* ctx, const double* lam_dev, const double* x_dev, int k, double* out_host);
 
 /* Spectral diagnostics.  MINRES is the Lanczos process on M^{-1} K in the
@@ -277,7 +281,10 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * entries split by the level of their column: a level sums the entries of
  * levels two or more steps back before it waits for the level just before it,
  * and releases the next level only after that wait; about 12 / 32 entries per
- * lane).
+ * lane), 9 SELL-32 with 1 / 2 / 4 / 8 warps per 32-row slice chosen per level
+ * from its longest row (every lane loads up to 12 of its slots before the
+ * wait for the previous level and then gathers all its solution entries at
+ * once).
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside

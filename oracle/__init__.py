@@ -61,13 +61,14 @@ def lib():
             for name in ("or_sizes", "or_csr", "or_wmean", "or_perm", "or_load_fourier",
                          "or_load_manufactured", "or_manufactured_errors", "or_minres", "or_load_cavity",
                          "or_pcg", "or_precond", "or_stokes_apply", "or_filter", "or_perm_q",
-                         "or_pcg_q"):
+                         "or_pcg_q", "or_colours"):
                 getattr(L, name).restype = i32
             L.or_sizes.argtypes = [vp, vp]
             L.or_csr.argtypes = [vp, i32, vp, vp, vp]
             L.or_wmean.argtypes = [vp, vp]
             L.or_perm.argtypes = [vp, vp, vp, vp]
             L.or_perm_q.argtypes = [vp, vp, vp, vp]
+            L.or_colours.argtypes = [vp, vp]
             L.or_factor.restype = i64
             L.or_factor.argtypes = [vp]
             L.or_factor_q.restype = i64
@@ -185,6 +186,13 @@ class Problem:
         rlev = np.zeros(self.n_u, np.int32)
         lib().or_perm(self._h, _p(perm), _p(lev), _p(rlev))
         return perm, lev, rlev
+
+    def colours(self):
+        """Colour of every velocity DOF (natural numbering) under the
+        multicolour rule: (component, index mod (degree + 1) per direction)."""
+        out = np.zeros(self.n_u, np.int64)
+        lib().or_colours(self._h, _p(out))
+        return out
 
     def ordering_arrays_q(self):
         """Ordering of the pressure space before IC(0) of Q: (perm, level, rlevel)."""

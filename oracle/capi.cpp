@@ -136,6 +136,14 @@ int or_perm(void* hv, int32_t* perm, int32_t* level, int32_t* rlevel) {
   return 0;
 }
 
+// Colour of every velocity DOF (natural numbering) under the multicolour
+// rule, whatever ordering the problem uses.
+int or_colours(void* hv, int64_t* out) {
+  Handle* h = static_cast<Handle*>(hv);
+  for (int64_t i = 0; i < h->P.n_u; ++i) out[i] = velocity_colour(h->P, i);
+  return 0;
+}
+
 int or_perm_q(void* hv, int32_t* perm, int32_t* level, int32_t* rlevel) {
   Handle* h = static_cast<Handle*>(hv);
   int64_t n = h->P.n_p;

@@ -98,6 +98,8 @@ void manufactured_point(double nu, double x, double y, double out[5]);
 // -------------------------------------------------------------- ordering.cpp
 // perm[new] = old.  kind 0 natural, 1 reverse Cuthill-McKee, 2 multicolour.
 void make_ordering(const Problem& P, int kind, std::vector<int32_t>& perm);
+// Colour of velocity DOF i (natural numbering) in the multicolour ordering.
+int64_t velocity_colour(const Problem& P, int64_t i);
 // The same three orderings of the pressure space, applied to Q before its
 // IC(0) (Sec. 6.4 reorders A and Q separately by reverse Cuthill-McKee).
 void make_pressure_ordering(const Problem& P, int kind, std::vector<int32_t>& perm);

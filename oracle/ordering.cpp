@@ -102,20 +102,22 @@ static void rcm(const Csr& A, std::vector<int32_t>& perm) {
 // one component couple in A only if |l_k - l'_k| <= deg(c,k) in every
 // direction, so DOFs of one colour are mutually uncoupled.  Order: by colour,
 // then by natural index.
+int64_t velocity_colour(const Problem& P, int64_t i) {
+  int c, a[3] = {0, 0, 0};
+  P.vdecode(i, &c, a);
+  int64_t col = c;
+  for (int k = 0; k < P.dim; ++k) {
+    int m = P.deg(c, k) + 1;
+    int l = (k == c) ? a[k] - 1 : a[k];
+    col = col * m + (l % m);
+  }
+  return col;
+}
+
 static void multicolour(const Problem& P, std::vector<int32_t>& perm) {
   const int64_t n = P.n_u;
   std::vector<int64_t> colour(n);
-  for (int64_t i = 0; i < n; ++i) {
-    int c, a[3] = {0, 0, 0};
-    P.vdecode(i, &c, a);
-    int64_t col = c;
-    for (int k = 0; k < P.dim; ++k) {
-      int m = P.deg(c, k) + 1;
-      int l = (k == c) ? a[k] - 1 : a[k];
-      col = col * m + (l % m);
-    }
-    colour[i] = col;
-  }
+  for (int64_t i = 0; i < n; ++i) colour[i] = velocity_colour(P, i);
   perm.resize(n);
   for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
   std::stable_sort(perm.begin(), perm.end(),

@@ -274,7 +274,7 @@ class Stokes:
         return out
 
     LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4, "packed12": 5,
-               "packed32": 6, "split12": 7, "split32": 8}
+               "packed32": 6, "split12": 7, "split32": 8, "sellw": 9}
     SPMV_LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "sell2w": 2, "sell4w": 3}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
@@ -284,7 +284,8 @@ class Stokes:
         'staged12', 'staged32': rows staged in shared memory, 'packed12',
         'packed32': k-major copies, 'split12', 'split32': k-major copies
         whose older-level entries are summed before the wait for the
-        previous level), or 'auto'."""
+        previous level), 'sellw' (SELL-32 with 1-8 warps per slice by the
+        level's longest row, every slot loaded before the wait), or 'auto'."""
         _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.SPMV_LAYOUTS[spmv],
                                                       self.LAYOUTS[trsv]))
 

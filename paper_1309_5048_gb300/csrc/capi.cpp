@@ -253,7 +253,8 @@ int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double*
 }
 
 int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
-  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 8) {
+  if (!h) return bad_arg("null context");
+  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 9) {
     set_error("bad kernel variant request");
     return GB_ERR_INVALID_ARG;
   }
@@ -268,6 +269,7 @@ int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
 }
 
 int gb_set_batch_sweep(gb_ctx* h, int precision, int width, int variant) {
+  if (!h) return bad_arg("null context");
   if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || variant < -1 || variant > 1) {
     set_error("bad batch sweep request");
     return GB_ERR_INVALID_ARG;
@@ -278,6 +280,7 @@ int gb_set_batch_sweep(gb_ctx* h, int precision, int width, int variant) {
 }
 
 int gb_get_batch_sweep(const gb_ctx* h, int precision, int width, int* variant) {
+  if (!h) return bad_arg("null context");
   if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || !variant) {
     set_error("bad batch sweep query");
     return GB_ERR_INVALID_ARG;
@@ -287,6 +290,7 @@ int gb_get_batch_sweep(const gb_ctx* h, int precision, int width, int* variant) 
 }
 
 int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv) {
+  if (!h) return bad_arg("null context");
   if (!h || precision < 0 || precision > 1 || !spmv || !trsv) {
     set_error("bad kernel variant query");
     return GB_ERR_INVALID_ARG;

@@ -231,6 +231,7 @@ struct Ctx {
   bool q_factored = false;
   Sell sA, sL, sU;                 // SELL-32 copies of A, L, U
   std::vector<int32_t> lev_slice;  // level l = slices [lev_slice[l], lev_slice[l+1])
+  std::vector<int32_t> lev_maxL, lev_maxU;  // longest off-diagonal row of L, U in level l
   Staged tL, tU;                   // staged-sweep partitions of L and U = L^T
   Packed pL, pU;                   // packed (k-major) copies of L and U
   Packed qL, qU;                   // the same, each row split by the level of its columns

@@ -25,8 +25,8 @@ void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col
   S.row0.upload(h.row0.data(), h.row0.size(), stream);
   S.off.upload(h.off.data(), h.off.size(), stream);
   S.rowlen.upload(h.rowlen.data(), h.rowlen.size(), stream);
-  S.col.upload(h.col.data(), std::max<size_t>(1, h.col.size()), stream);
-  S.src.upload(h.src.data(), std::max<size_t>(1, h.src.size()), stream);
+  S.col.upload(h.col.data(), h.col.size(), stream);  // empty: one slot, no copy
+  S.src.upload(h.src.data(), h.src.size(), stream);
   S.val.alloc(std::max<int64_t>(1, h.slots));
   S.val32.alloc(std::max<int64_t>(1, h.slots));
 }
@@ -63,8 +63,8 @@ void build_packed(const std::vector<int32_t>& ptr, const std::vector<int32_t>& c
   T.desc.upload(h.desc.data(), h.desc.size(), stream);
   Sell& S = T.data;
   S.slots = (int64_t)h.col.size();
-  S.col.upload(h.col.data(), std::max<size_t>(1, h.col.size()), stream);
-  S.src.upload(h.src.data(), std::max<size_t>(1, h.src.size()), stream);
+  S.col.upload(h.col.data(), h.col.size(), stream);  // empty: one slot, no copy
+  S.src.upload(h.src.data(), h.src.size(), stream);
   S.val.alloc(std::max<int64_t>(1, S.slots));
   S.val32.alloc(std::max<int64_t>(1, S.slots));
 }
@@ -173,6 +173,13 @@ void setup_pattern(Ctx& c, const gb_problem& prob) {
   c.max_lrow = 0;
   for (int64_t r = 0; r < n; ++r)
     c.max_lrow = std::max({c.max_lrow, Lptr[r + 1] - Lptr[r], Uptr[r + 1] - Uptr[r]});
+  c.lev_maxL.assign(c.nlev, 0);
+  c.lev_maxU.assign(c.nlev, 0);
+  for (int l = 0; l < c.nlev; ++l)
+    for (int32_t r = c.lev_ptr[l]; r < c.lev_ptr[l + 1]; ++r) {
+      c.lev_maxL[l] = std::max(c.lev_maxL[l], Lptr[r + 1] - Lptr[r]);
+      c.lev_maxU[l] = std::max(c.lev_maxU[l], Uptr[r + 1] - Uptr[r]);
+    }
   c.status_d.alloc(16);
   c.status_d.zero(s);
   GBS_CUDA(cudaStreamSynchronize(s));

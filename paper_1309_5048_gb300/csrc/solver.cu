@@ -366,8 +366,34 @@ struct Run {
                                 std::max(c.qL.cap, c.qU.cap), std::max(c.qL.rcap, c.qU.rcap),
                                 (const int4*)pk.desc.p + (has ? pk.lev_b[ln] : 0), has ? pk.lev_nb[ln] : 0));
   }
+  // SELL-32 sweep with W warps per slice: W from the level's longest row,
+  // so that kSellwPF slots per lane cover it.
+  template <bool FWD, int W>
+  void sellw_level(cudaLaunchConfig_t& cfg, int l) {
+    const int s0 = c.lev_slice[l], s1 = c.lev_slice[l + 1];
+    constexpr int SPB = kBlock / (32 * W);
+    cfg.gridDim = dim3((unsigned)std::max(1, (s1 - s0 + SPB - 1) / SPB));
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, kSellwPF>, a, s0, s1));
+  }
   template <bool FWD>
   void level(int l) {
+    if (K == 1 && vtrsv == 9) {
+      const int len = FWD ? c.lev_maxL[l] : c.lev_maxU[l];
+      cudaLaunchConfig_t cfg = {};
+      cfg.blockDim = dim3(kBlock);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (len <= kSellwPF) sellw_level<FWD, 1>(cfg, l);
+      else if (len <= 2 * kSellwPF) sellw_level<FWD, 2>(cfg, l);
+      else if (len <= 4 * kSellwPF) sellw_level<FWD, 4>(cfg, l);
+      else sellw_level<FWD, 8>(cfg, l);
+      return;
+    }
     if (K == 1 && vtrsv >= 7) {
       const Packed& pk = FWD ? c.qL : c.qU;
       const float per_lane = vtrsv == 7 ? 12.f : 32.f;
@@ -755,7 +781,7 @@ void autotune_single(Ctx& c) {
   if (c.var_trsv[pi] < 0) {
     float best = time_it(0, 1);
     int choice = 0;
-    for (int v = 1; v <= 8; ++v) {
+    for (int v = 1; v <= 9; ++v) {
       if (!trsv_available(c, v)) continue;
       const float t = time_it(v, 1);
       if (t < 0.97f * best) {
@@ -1148,17 +1174,17 @@ void dnu(Ctx& c, const double* lam, const double* x, int k, double* out) {
 
 // ---- dL/dnu without allocating device memory --------------------------------
 // gb_dnu may allocate the context's workspace (cudaMalloc) on first use.  Some
-// callers cannot allow that: code that runs while a CUDA graph is being
-// captured, programs whose device memory is owned by a pool or framework that
-// forbids further cudaMalloc calls, and callers that have used up a fixed
-// memory budget.  dnu_noalloc computes the same quantity with the same kernel
-// (k_dnu, same launch) but takes its reduction scratch -- the per-block
-// partial sums, the completion counter and the k results -- from the static
-// device array below, whose size is fixed at build time: 64 + 1216 * 32
-// doubles (about 304 KiB), enough for the largest launch (1216 blocks) and
-// k <= 32.  Every GPU that loads this library holds the array until the
-// process exits.  All calls share it, so calls that overlap on the GPU race;
-// each call clears the counter before its launch.
+// callers cannot allow that: programs whose device memory is handed out by
+// their own pool or framework, which forbids raw allocations beside it, and
+// callers that have used up a fixed memory budget.  dnu_noalloc computes the
+// same quantity with the same kernel (k_dnu, same launch) but takes its
+// reduction scratch -- the per-block partial sums, the completion counter and
+// the k results -- from the static device array below, whose size is fixed at
+// build time: 64 + 1216 * 32 doubles (about 304 KiB), enough for the largest
+// launch (1216 blocks) and k <= 32.  Every GPU that loads this library holds
+// the array until the process exits.  All calls share it, so calls that
+// overlap on the GPU race; each call clears the counter before its launch.
+// The call ends by copying the k results to host memory and waiting for them.
 constexpr int kNoAllocMaxK = 32;
 constexpr size_t kNoAllocDoubles = 64 + (size_t)kRB * kNoAllocMaxK;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];

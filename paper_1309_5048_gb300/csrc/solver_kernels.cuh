@@ -29,6 +29,7 @@ namespace gbs {
 namespace {
 
 constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
+constexpr int kSellwPF = 12;  // slots per lane loaded before the wait by k_trsv_level_sellw
 
 // Device view of a SELL-32 matrix copy (see Sell in gbs_internal.h).
 struct SellView {
@@ -932,6 +933,75 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
     if (k < len) sum += v[k] * __ldcg(out + cc[k]);
   for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
   if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
+}
+
+// One level of a triangular solve on the SELL-32 copy with W warps per
+// 32-row slice (same recurrences as k_trsv_level).  Warp h of a slice owns the
+// stencil slots k = h, h + W, ... of its 32 rows; before the wait for the
+// previous level each lane loads the column indices and factor values of its
+// first PF slots (coalesced: a warp reads one slot of 32 neighbouring rows),
+// with the streaming cache hint so that the factor, read once per sweep, does
+// not push the solution vector out of L2.  After the wait every lane issues
+// the gathers of all its solution entries at once -- one L2 round trip per
+// level -- and sums value * entry in slot order; the W partial sums of a row
+// are then added in warp order in shared memory.  The host picks W per level
+// so that PF slots per lane cover the level's longest row (slots beyond PF, if
+// any, are read after the wait).  One thread per row and lane keeps the FP64
+// issue at one DFMA per entry plus W - 1 DADDs per row.
+template <class T, bool FWD, int W, int PF>
+__global__ void __launch_bounds__(kBlock, 4) k_trsv_level_sellw(Args a, int s0, int s1) {
+  constexpr int SPB = kBlock / (32 * W);  // slices per block
+  static_assert(SPB * 32 * W == kBlock, "block shape");
+  __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
+  cudaTriggerProgrammaticLaunchCompletion();
+  const SellView m = FWD ? a.sL : a.sU;
+  const T* __restrict__ val = pick<T>(m.val, m.val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = warp % W, ls = warp / W;
+  const int s = s0 + blockIdx.x * SPB + ls;
+  int row = -1, n = 0, base = 0;
+  int cc[PF];
+  T v[PF];
+  T ii = T(0);
+  if (s < s1) {
+    const int r = m.row0[s] + lane;
+    if (r < m.row0[s + 1]) {
+      row = r;
+      const int len = m.rowlen[r];
+      n = len > h ? (len - h + W - 1) / W : 0;  // slots h, h + W, ... below len
+      base = m.off[s] + 32 * h + lane;
+      if (h == 0) ii = inv[r];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    cc[u] = u < n ? __ldcs(m.col + base + 32 * W * u) : 0;
+    v[u] = u < n ? __ldcs(val + base + 32 * W * u) : T(0);
+  }
+  cudaGridDependencySynchronize();
+  T xg[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
+  T sum = 0;
+#pragma unroll
+  for (int u = 0; u < PF; ++u)
+    if (u < n) sum += v[u] * xg[u];
+  for (int u = PF; u < n; ++u) sum += __ldcs(val + base + 32 * W * u) * __ldcg(out + __ldcs(m.col + base + 32 * W * u));
+  if (W > 1) {
+    if (h > 0) part[h - 1][ls][lane] = sum;
+    __syncthreads();
+    if (h == 0) {
+#pragma unroll
+      for (int u = 0; u < W - 1; ++u) sum += part[u][ls][lane];
+    }
+  }
+  if (h == 0 && row >= 0) {
+    const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the store only
+    if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
+  }
 }
 
 // ---- staged variant (single right-hand side) ------------------------------

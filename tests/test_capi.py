@@ -97,8 +97,17 @@ def test_every_entry_point_rejects_a_null_context(lib):
             continue
         f = getattr(L, name)
         args = [1.0 if t is C.c_double else (1 if t in (C.c_int, C.c_int64) else None) for t in f.argtypes]
+        # the message is thread-local and sticky: first leave a different one
+        # (gb_setup_pattern and gb_sizes say "null argument", gb_assemble
+        # "null context"), so each call must write its own
+        if name in ("gb_setup_pattern", "gb_sizes"):
+            assert L.gb_assemble(None, 1.0, 1.0) == 1
+        else:
+            assert L.gb_setup_pattern(None, None, None) == 1
+        before = L.gb_last_error()
         assert f(*args) == 1, name
-        assert L.gb_last_error(), name
+        after = L.gb_last_error()
+        assert b"null" in after and after != before, name
     L.gb_destroy(None)
     codes = [L.gb_status_string(k) for k in range(8)]
     assert len(set(codes)) == 8 and all(codes)

@@ -327,7 +327,8 @@ def test_edge_cases(oracle_mod, gb):
 
 LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr"), ("csr", "staged4"),
                 ("sell", "staged12"), ("csr", "staged32"), ("csr", "packed12"), ("sell", "packed32"),
-                ("sell2w", "packed32"), ("sell4w", "csr"), ("csr", "split12"), ("sell2w", "split32")]
+                ("sell2w", "packed32"), ("sell4w", "csr"), ("csr", "split12"), ("sell2w", "split32"),
+                ("sell", "sellw"), ("sell2w", "sellw")]
 
 
 @pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
@@ -335,8 +336,9 @@ LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr
 def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p):
     """Every single-RHS layout of the inner SpMV (CSR 8 lanes per row,
     SELL-32 thread per row) and of the IC(0) sweeps (also the staged and
-    packed forms, whose levels are split over many blocks at 2D 40^2)
-    reproduces the oracle (<= 1e-10)."""
+    packed forms, whose levels are split over many blocks at 2D 40^2, and the
+    SELL form with several warps per slice, whose rows in 3D and at degree 4
+    are longer than its prefetch) reproduces the oracle (<= 1e-10)."""
     ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
     assert ref.factor() < 0
     s.factor_ic0()
@@ -360,7 +362,7 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     s.solve(rhs, tol=1e-6)
     spmv, trsv = s.kernel_variants("fp64")
     assert spmv in ("csr", "sell", "sell2w", "sell4w") and trsv in ("csr", "sell", "staged4", "staged12", "staged32", "packed12",
-                                                 "packed32", "split12", "split32")
+                                                 "packed32", "split12", "split32", "sellw")
 
 
 @pytest.mark.slow

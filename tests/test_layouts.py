@@ -254,3 +254,22 @@ def test_sell_copies(oracle_mod, lt, dim, N, p, ordering):
         assert np.array_equal(expect, ssrc)
         real = ssrc >= 0
         assert np.array_equal(scol[real], col[ssrc[real]])
+
+
+def test_a_diagonal_only_factor_gives_empty_copies(lt):
+    """A factor with no strict entries (one level of 70 rows, every row empty):
+    the SELL copy has no slots and the packed copy no slots, and both still
+    tile the level, so the upload sends no entry and reads nothing past the
+    empty host vectors."""
+    n = 70
+    ptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(1, np.int32)  # a valid pointer for an empty vector
+    lev_ptr = np.array([0, n], np.int32)
+    row0, off, rowlen, scol, ssrc, lev_slice = sell(lt, ptr, col[:0], lev_ptr)
+    assert len(scol) == 0 and len(ssrc) == 0 and np.all(rowlen == 0)
+    assert row0[lev_slice[0]] == 0 and row0[lev_slice[1]] == n
+    assert np.all(off == 0)
+    for split in (0, 1):
+        lay = packed(lt, ptr, col[:0], lev_ptr, 152, split)
+        assert lay is not None and len(lay["col"]) == 0 and len(lay["src"]) == 0
+        check_packed(lay, ptr, col[:0], lev_ptr, 152, split)

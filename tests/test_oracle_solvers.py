@@ -325,3 +325,44 @@ def test_minres_every_block_reaches_the_direct_solution(oracle_mod, velocity, pr
                        velocity=velocity, pressure=pressure)
     assert info["status"] == 0 and info["relres_true"] <= 1e-12
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+
+
+# 3D at degree 6 is left out: the oracle's element assembly alone takes two
+# minutes there, and the colour rule is the same code for every degree.
+@pytest.mark.parametrize("dim,N,p", [(2, 4, 2), (2, 4, 3), (2, 4, 4), (2, 5, 5), (2, 5, 6),
+                                     (3, 3, 2), (3, 3, 3), (3, 3, 4), (3, 3, 5)])
+def test_multicolour_classes_are_uncoupled_and_counted_by_the_degrees(oracle_mod, dim, N, p):
+    """The multicolour ordering (a reading of the paper's reordering before
+    IC(0), Sec. 6.4) lists the velocity DOFs colour by colour, each colour in
+    natural order, and no two DOFs of one colour couple in A_h.  Velocity
+    component c has degree p in direction c and p - 1 in the others (Sec.
+    3.2); two of its B-splines of degree q overlap only when their indices
+    differ by at most q in every direction, so a class per (component, index
+    mod (degree + 1) per direction) is uncoupled, and dim (p + 1) p^(dim - 1)
+    classes are needed once every residue occurs.  Checked against A_h as
+    assembled: no nonzero couples two DOFs of one colour (a smaller modulus
+    breaks this); the colour count is the formula and the class sizes are the
+    products of the residue counts (a larger modulus gives more, smaller
+    classes); the ordering is sorted by colour, then by natural index."""
+    P = oracle_mod.Problem(dim, N, p, ordering="multicolour")
+    colour = P.colours()
+    A = P.scipy("A").tocoo()
+    off = A.row != A.col
+    assert np.all(colour[A.row[off]] != colour[A.col[off]])
+    assert len(np.unique(colour)) == dim * (p + 1) * p ** (dim - 1)
+    perm, _, _ = P.ordering_arrays()
+    key = colour[perm] * P.n_u + perm
+    assert np.all(np.diff(key) > 0)
+    m = N + p - 1  # functions per direction of degree p - 1 (full space)
+    expect = []
+    for c in range(dim):
+        counts = []
+        for k in range(dim):
+            # degree p in direction c: N + p functions minus the two with a normal trace
+            nf, mod = (m - 1, p + 1) if k == c else (m, p)
+            counts.append([len(range(r0, nf, mod)) for r0 in range(mod)])
+        for idx in np.ndindex(*[len(cc) for cc in counts]):
+            expect.append(int(np.prod([counts[k][idx[k]] for k in range(dim)])))
+    assert sorted(np.unique(colour, return_counts=True)[1].tolist()) == sorted(expect)
