@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--all-variants", action="store_true",
+                    help="also the 3D 48^3 x 32 batches with the Diag(Q_nu) pressure block")
     ap.add_argument("--e2e-steps", type=int, default=2,
                     help="solves timed end to end through gb_solve_host (each one a full solve)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -542,6 +544,11 @@ VARIANTS = [
     ("mixed_k1_pcgq", None, "mixed", 1, "pcg", None, None),
     ("3d48_fp64_k32_pcgq", "3d48", "fp64", 32, "pcg", None, None),
     ("3d48_mixed_k32_pcgq", "3d48", "mixed", 32, "pcg", None, None),
+]
+# with --all-variants (each about a minute: with Diag(Q_nu) the batch runs
+# until its slowest forcing has converged, 230+ MINRES steps in 3D)
+EXTRA_VARIANTS = [
+    ("3d48_fp64_k32", "3d48", "fp64", 32, "diag", None, None),
     ("3d48_mixed_k32", "3d48", "mixed", 32, "diag", None, None),
 ]
 
@@ -696,7 +703,7 @@ def main():
     variants = {}
     if not args.no_variants and rank == 0:
         others = {}
-        for name, wl, prec, kk, pres, itol, cap in VARIANTS:
+        for name, wl, prec, kk, pres, itol, cap in VARIANTS + (EXTRA_VARIANTS if args.all_variants else []):
             Wv = WORKLOADS[wl] if wl else W
             if wl and wl != args.workload:
                 if wl not in others:

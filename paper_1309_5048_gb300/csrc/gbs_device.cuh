@@ -26,8 +26,11 @@ __device__ __forceinline__ float warp_sumf(float v) {
 // have left a loop or returned.
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
-  if (G == 32) return 0xffffffffu;
-  return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  if constexpr (G == 32) {
+    return 0xffffffffu;
+  } else {
+    return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  }
 }
 
 // Sum over the lane's group of G consecutive lanes.

@@ -132,24 +132,24 @@ def test_full_size_solution_properties(oracle_mod, gb, name, precision):
 
 def test_full_size_3d48_batched_and_adjoint(gb):
     """3D 48^3: a batch of 32 forcings in one graph launch (FP32 inner
-    preconditioner), every column meeting the tolerance and its true residual;
-    then the adjoint for L = 1/2 ||u - u_t||^2 against its closed form.
+    preconditioner, Diag(Q_nu) pressure block), every column meeting the
+    contract tolerance 1e-8 on its 2-norm relative residual ||b - K x|| / ||b||
+    (the stopping rule, carried by a recurrence on the device and recomputed
+    here from the true residual); then the adjoint for L = 1/2 ||u - u_t||^2
+    against its closed form.
 
     A_h is 2 nu times a nu-free matrix and B does not depend on nu, so
     u(nu) = u(1) / nu and dL/dnu = -(u - u_t)^T u / nu exactly (the oracle
-    test of the adjoint pins the same identity at small size). The batch stops
-    at 1e-6: with the diagonal pressure block and a relaxed inner solve, some
-    3D forcings need thousands of steps to 1e-8 (and stall in the
-    |eta| / gamma_1 estimate while their 2-norm residual is an order lower)."""
+    test of the adjoint pins the same identity at small size)."""
     from paper_1309_5048_gb300.inputs import target_velocity
     s = problem(gb, "3d48")
     R = _rhs(s, 32, 0)
-    X, infos = s.solve(R, tol=1e-6, inner_tol=1e-2, precision="mixed")
-    assert all(i["status"] == 0 and i["relres_true"] <= 1.01e-6 for i in infos)
+    X, infos = s.solve(R, tol=1e-8, inner_tol=1e-2, precision="mixed")
+    assert all(i["status"] == 0 and i["relres_true"] <= 1.01e-8 for i in infos)
     for t in (0, 13, 31):
         r = R[t] - s.apply("K", X[t])
         rel = float(r.norm() / R[t].norm())
-        assert rel <= 1.01e-6
+        assert rel <= 1.01e-8
         assert abs(rel - infos[t]["relres_true"]) <= 1e-3 * rel
     # adjoint of one column, FP64 solves: dL/dnu = -lambda_u^T A_0 u
     x0, i0 = s.solve(R[1], tol=1e-9, inner_tol=1e-2)
