@@ -54,8 +54,10 @@ extern "C" {
 #define GB_ERR_IC0_BREAKDOWN 4  /* IC(0) met a non-positive pivot */
 #define GB_ERR_NOT_CONVERGED 5  /* iteration cap reached; outputs written */
 #define GB_ERR_NONFINITE 6      /* NaN/Inf met in the right-hand side or iterates */
-#define GB_ERR_DEVICE_TIMEOUT 7 /* reserved: a bounded device wait gave up (no kernel
-                                   of this version waits on another one) */
+#define GB_ERR_DEVICE_TIMEOUT 7 /* a bounded device wait gave up: the TMA-staged sweep
+                                   (layout 10) waits on the completion of its own
+                                   bulk copies with a 2 s limit; no kernel waits
+                                   on another kernel or block */
 
 /* Orderings of A_h applied before IC(0).  The paper reorders A by reverse
  * Cuthill-McKee (Sec. 6.4); natural and multicolour orderings are offered
@@ -283,12 +285,22 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * and releases the next level only after that wait; about 12 / 32 entries per
  * lane), 9 SELL-32 with 1 / 2 / 4 / 8 warps per 32-row slice chosen per level
  * from its longest row (every lane loads up to 12 of its slots before the
- * wait for the previous level and then gathers all its solution entries at
- * once).
+ * wait for the previous level and then gathers them at once), 10 the same
+ * slice groups streamed into shared memory by bulk copies (cp.async.bulk with
+ * an mbarrier), two stages per block, the first two groups fetched before the
+ * wait (available when every factor row has at most 88 off-diagonal entries:
+ * 2D with velocity degree 3), 11 the SELL form of 9 with four slots loaded
+ * before the wait and the rest read in a loop (W for about 16 slots per lane;
+ * few registers, many warps per SM), 12 the same with about 8 slots per lane,
+ * 13 the form of 11 on a grid of the resident blocks, each taking several
+ * slice groups of a level in turn.  Layouts 1 and 9 - 13 also carry the CG
+ * step of the inner solve: the forward sweep reduces rho = r^T z as
+ * ||L^{-1} r||^2 and the backward sweep updates the search direction.
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside
- * these ranges return GB_ERR_INVALID_ARG, and so do trsv 2 - 8 when a row of
+ * these ranges return GB_ERR_INVALID_ARG, and so do trsv 10 when a factor row
+ * has more than 88 off-diagonal entries and trsv 2 - 8 when a row of
  * the factor has more than 2048 off-diagonal entries (3D with velocity degree
  * 5 or 6 on all but the coarsest meshes): those layouts are then not built,
  * and the automatic choice skips them.  gb_get_kernel_variants reports the

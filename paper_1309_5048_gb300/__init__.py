@@ -274,7 +274,7 @@ class Stokes:
         return out
 
     LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4, "packed12": 5,
-               "packed32": 6, "split12": 7, "split32": 8, "sellw": 9}
+               "packed32": 6, "split12": 7, "split32": 8, "sellw": 9, "tma": 10, "sellwl": 11, "sellwl8": 12, "sellwlr": 13}
     SPMV_LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "sell2w": 2, "sell4w": 3}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
@@ -285,7 +285,14 @@ class Stokes:
         'packed32': k-major copies, 'split12', 'split32': k-major copies
         whose older-level entries are summed before the wait for the
         previous level), 'sellw' (SELL-32 with 1-8 warps per slice by the
-        level's longest row, every slot loaded before the wait), or 'auto'."""
+        level's longest row, up to 12 slots per lane loaded before the wait),
+        'tma' (the same slice groups streamed into shared memory by bulk
+        copies, double-buffered; rows of at most 88 entries: 2D, velocity
+        degree 3), 'sellwl' (the SELL form with four slots loaded before the
+        wait and the rest read in a loop, about 16 slots per lane), 'sellwl8'
+        (the same with about 8 slots per lane), 'sellwlr' (the light form on
+        a grid of the resident blocks, each taking several slice groups), or
+        'auto'."""
         _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.SPMV_LAYOUTS[spmv],
                                                       self.LAYOUTS[trsv]))
 

@@ -76,6 +76,11 @@ enum ScalarField {
 // off[s] + 32 k + i.  rowlen[row] bounds each row (padding is never read);
 // src maps every slot to the position of its value in the CSR value array
 // (-1 for padding), so values are refilled after assembly / factorisation.
+// Slots per lane and slice group of the TMA-staged SELL sweep: a level whose
+// longest factor row exceeds 8 * kTmaPF has no group that fits a stage, so
+// that layout is available only when every row of L and U is that short.
+constexpr int kTmaPF = 11;
+
 struct Sell {
   DevBuf<int32_t> off, row0, rowlen, col, src;
   DevBuf<double> val;
@@ -141,6 +146,7 @@ struct Workspace {
   double* W[3] = {nullptr, nullptr, nullptr};
   double* q = nullptr;
   double* b = nullptr;  // right-hand side, internal layout
+  double* rho_part = nullptr;  // per-block partials of rho = ||L^{-1} r||^2 over a forward sweep
   double* R = nullptr;  // residual b - K x_j (2-norm stopping rule)
   double* lz = nullptr;  // Lanczos tridiagonal record [2][K][lz_cap]
   int lz_cap = 0;
@@ -247,7 +253,9 @@ struct Ctx {
   // warp-per-row kernel, 1 the staged batched kernel, -1 not chosen yet
   int var_trsv_batch[2][2] = {{-1, -1}, {-1, -1}};
   int max_lrow = 0;  // longest off-diagonal row of L and U
-  DevBuf<int> status_d;  // device error flags
+  DevBuf<int> status_d;  // device error flags: [0] IC(0) breakdown row, [1] band Cholesky, [2] sweep wait timeout
+  DevBuf<int32_t> tune_forced;  // replay counts of the in-graph layout tuning solve
+  int tma_bps[2] = {0, 0};  // resident blocks per SM of the TMA sweep (FP64, FP32), 0: not yet known
   double nu = 1.0, cpen = 0.0;
   bool assembled = false, factored = false;
   Workspace ws;

@@ -201,6 +201,7 @@ bool trsv_available(const Ctx& c, int v) {
   if (v >= 2 && v <= 4) return c.tL.ok && c.tU.ok;
   if (v >= 5 && v <= 6) return c.pL.ok && c.pU.ok;
   if (v >= 7 && v <= 8) return c.qL.ok && c.qU.ok;
+  if (v == 10) return c.max_lrow <= 8 * kTmaPF;
   return true;
 }
 

@@ -68,6 +68,9 @@ void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
     w.flag = (int*)dmalloc(sizeof(int) * 8);
     GBS_CUDA(cudaMallocHost((void**)&w.flag_host, sizeof(int) * 8));
     w.partial = (double*)dmalloc(sizeof(double) * kRB * 32 * 4);
+    // one partial per block of a forward sweep of the SELL-family layouts
+    // (a level's grid never exceeds its slice count)
+    w.rho_part = (double*)dmalloc(sizeof(double) * ((size_t)c.sL.nslices + c.nlev + 1));
     w.counter = (unsigned*)dmalloc(64);
     w.aux = (double*)dmalloc(sizeof(double) * kRB * 32);
     GBS_CUDA(cudaMemsetAsync(w.counter, 0, 64, c.stream));
@@ -175,6 +178,8 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.R = w.R;
   a.lz = w.lz;
   a.lz_cap = w.lz_cap;
+  a.dev_status = c.status_d.p + 2;
+  a.rho_part = w.rho_part;
   a.KW0 = w.KW[0];
   a.KW1 = w.KW[1];
   a.KW2 = w.KW[2];
@@ -295,8 +300,42 @@ void batch_allow_smem(const Ctx& c) {
   GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_batch<K, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
 }
 
+// Dynamic shared memory of k_trsv_level_tma: two stages of values and column
+// indices, then two mbarriers (one size for every launch).
+template <class T>
+size_t tma_bytes() {
+  return (size_t)2 * kTmaCap * (sizeof(T) + 4) + 2 * sizeof(uint64_t);
+}
+
+template <class T, bool FWD, int W>
+void tma_allow_smem_one() {
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_tma<T, FWD, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tma_bytes<T>()));
+  GBS_CUDA(cudaFuncSetAttribute(k_trsv_level_tma<T, FWD, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+}
+
+template <class T>
+void tma_prepare(Ctx& c) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  if (c.tma_bps[pi] > 0) return;
+  tma_allow_smem_one<T, true, 1>();
+  tma_allow_smem_one<T, true, 2>();
+  tma_allow_smem_one<T, true, 4>();
+  tma_allow_smem_one<T, true, 8>();
+  tma_allow_smem_one<T, false, 1>();
+  tma_allow_smem_one<T, false, 2>();
+  tma_allow_smem_one<T, false, 4>();
+  tma_allow_smem_one<T, false, 8>();
+  int bps = 0;  // the forward W = 8 form has the largest static shared memory
+  GBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_trsv_level_tma<T, true, 8>, kBlock,
+                                                         tma_bytes<T>()));
+  c.tma_bps[pi] = std::max(1, bps);
+}
+
 template <class T>
 void staged_prepare(Ctx& c) {
+  tma_prepare<T>(c);
   batch_allow_smem<8, T>(c);
   batch_allow_smem<32, T>(c);
   staged_allow_smem<T, true>(staged_bytes<T>(c));
@@ -329,6 +368,7 @@ struct Run {
   Args a;
   cudaStream_t s;
   int vspmv = 0, vtrsv = 0;  // single-RHS layouts (Ctx::var_spmv, Ctx::var_trsv)
+  int pbase = 0;             // partials of rho written so far in this forward sweep (fused CG step)
   int vbatch = 0;            // batched sweep (Ctx::var_trsv_batch)
   static constexpr int G = Map<K>::G;
   Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {
@@ -366,18 +406,38 @@ struct Run {
                                 std::max(c.qL.cap, c.qU.cap), std::max(c.qL.rcap, c.qU.rcap),
                                 (const int4*)pk.desc.p + (has ? pk.lev_b[ln] : 0), has ? pk.lev_nb[ln] : 0));
   }
-  // SELL-32 sweep with W warps per slice: W from the level's longest row,
-  // so that kSellwPF slots per lane cover it.
-  template <bool FWD, int W>
-  void sellw_level(cudaLaunchConfig_t& cfg, int l) {
+  // SELL-32 sweeps with W warps per slice (k_trsv_level_sellw): W from the
+  // level's longest row; with `resident` a grid of at most the resident
+  // blocks, each taking several slice groups.
+  template <bool FWD, int W, int PF>
+  void sellw_level(cudaLaunchConfig_t& cfg, int l, bool resident = false) {
     const int s0 = c.lev_slice[l], s1 = c.lev_slice[l + 1];
     constexpr int SPB = kBlock / (32 * W);
-    cfg.gridDim = dim3((unsigned)std::max(1, (s1 - s0 + SPB - 1) / SPB));
-    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, kSellwPF>, a, s0, s1));
+    int grid = std::max(1, (s1 - s0 + SPB - 1) / SPB);
+    if (resident) grid = std::min(grid, c.n_sm * 5);  // the resident blocks of 256 threads (launch bounds: 5 per SM)
+    cfg.gridDim = dim3((unsigned)grid);
+    const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, PF>, a, s0, s1, pbase, pl));
+    if (FWD) pbase += grid;
+  }
+  // TMA-staged SELL sweep: W from the level's longest row, a grid of at
+  // most the resident blocks, each taking groups of 8 / W slices in turn.
+  template <bool FWD, int W>
+  void tma_level(cudaLaunchConfig_t& cfg, int l) {
+    const int s0 = c.lev_slice[l], s1 = c.lev_slice[l + 1];
+    constexpr int SPB = kBlock / (32 * W);
+    const int groups = std::max(1, (s1 - s0 + SPB - 1) / SPB);
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    const int grid = std::min(groups, c.n_sm * std::max(1, c.tma_bps[pi]));
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.dynamicSmemBytes = tma_bytes<T>();
+    const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_tma<T, FWD, W>, a, s0, s1, pbase, pl));
+    if (FWD) pbase += grid;
   }
   template <bool FWD>
   void level(int l) {
-    if (K == 1 && vtrsv == 9) {
+    if (K == 1 && vtrsv >= 9) {
       const int len = FWD ? c.lev_maxL[l] : c.lev_maxU[l];
       cudaLaunchConfig_t cfg = {};
       cfg.blockDim = dim3(kBlock);
@@ -388,10 +448,24 @@ struct Run {
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if (len <= kSellwPF) sellw_level<FWD, 1>(cfg, l);
-      else if (len <= 2 * kSellwPF) sellw_level<FWD, 2>(cfg, l);
-      else if (len <= 4 * kSellwPF) sellw_level<FWD, 4>(cfg, l);
-      else sellw_level<FWD, 8>(cfg, l);
+      if (vtrsv == 9) {
+        if (len <= kSellwPF) sellw_level<FWD, 1, kSellwPF>(cfg, l);
+        else if (len <= 2 * kSellwPF) sellw_level<FWD, 2, kSellwPF>(cfg, l);
+        else if (len <= 4 * kSellwPF) sellw_level<FWD, 4, kSellwPF>(cfg, l);
+        else sellw_level<FWD, 8, kSellwPF>(cfg, l);
+      } else if (vtrsv == 10) {
+        if (len <= kTmaPF) tma_level<FWD, 1>(cfg, l);
+        else if (len <= 2 * kTmaPF) tma_level<FWD, 2>(cfg, l);
+        else if (len <= 4 * kTmaPF) tma_level<FWD, 4>(cfg, l);
+        else tma_level<FWD, 8>(cfg, l);
+      } else {  // light form: about 16 (11, 13) or 8 (12) slots per lane; 13 on a resident grid
+        const int per = vtrsv == 12 ? 8 : 16;
+        const bool res = vtrsv == 13;
+        if (len <= per) sellw_level<FWD, 1, kSellwLitePF>(cfg, l, res);
+        else if (len <= 2 * per) sellw_level<FWD, 2, kSellwLitePF>(cfg, l, res);
+        else if (len <= 4 * per) sellw_level<FWD, 4, kSellwLitePF>(cfg, l, res);
+        else sellw_level<FWD, 8, kSellwLitePF>(cfg, l, res);
+      }
       return;
     }
     if (K == 1 && vtrsv >= 7) {
@@ -499,8 +573,14 @@ struct Run {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sell) GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sell<T, FWD>, a, r0, r1));
-    else GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
+    if (sell) {
+      const int grid = (int)cfg.gridDim.x;
+      const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
+      GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sell<T, FWD>, a, r0, r1, pbase, pl));
+      if (FWD) pbase += grid;
+    } else {
+      GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
+    }
   }
   void spmv() {
     if (K == 1 && vspmv == 2) k_cg_spmv_sellw<T, 2><<<grid_cap((int64_t)c.sA.nslices * 64), kBlock, 0, s>>>(a);
@@ -509,6 +589,7 @@ struct Run {
     else k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
   }
   void trsv_fwd() {
+    pbase = 0;
     for (int l = 0; l < c.nlev; ++l) level<true>(l);
   }
   void trsv_bwd() {
@@ -524,7 +605,19 @@ struct Run {
       trsv_bwd();
     }
   }
+  // The CG step rho = r^T z, beta, p = z + beta p runs inside the IC(0)
+  // sweeps of the SELL-family layouts (cg_fused_fwd_epilogue,
+  // cg_fused_bwd_store); the other layouts launch k_cg_rho and k_cg_pupdate.
+  bool fused_cg() const {
+    return K == 1 && a.velocity_block == GB_VELOCITY_IC0_PCG && (vtrsv == 1 || vtrsv >= 9);
+  }
   void cg_prologue() {
+    if (fused_cg()) {
+      a.cg_fuse = 2;
+      vel_precond();
+      a.cg_fuse = 0;
+      return;
+    }
     vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 1);
   }
@@ -533,6 +626,12 @@ struct Run {
     k_cg_axpy<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
   void cg_tail() {
+    if (fused_cg()) {
+      a.cg_fuse = 1;
+      vel_precond();
+      a.cg_fuse = 0;
+      return;
+    }
     vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 0);
     k_cg_pupdate<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
@@ -710,36 +809,89 @@ struct Run {
   }
 };
 
-// Layout tuning for single-RHS solves: time the CSR (8 lanes per row) and
-// SELL-32 (thread per row; 2 or 4 warps per slice) forms of the inner SpMV,
-// and the CSR, SELL-32,
-// three staged (about 4, 12, 32 entries per lane), two packed and two split
-// packed (about 12, 32 entries per lane) forms of one IC(0) application, on
-// this problem, and
-// keep the fastest; a form replaces the
-// best so far only when it is 3% faster.  Runs once per precision, outside
-// any graph capture; the choice only changes the summation order inside a row.
+// In-graph time of one single-RHS layout pair: a solve of one MINRES step
+// whose two preconditioner applications are forced (replay mode) to
+// kTuneInner inner iterations each, captured as the CUDA graph a solve runs --
+// SpMV, CG vector kernels, sweeps and MINRES kernels in their graph order,
+// each finding the L2 contents the previous one left -- launched once to warm
+// up, then timed over two launches.  rhs / out are the solve's own buffers
+// (out is overwritten by the solve that follows).
+constexpr int kTuneInner = 12;
+
 template <class T>
-void autotune_single(Ctx& c) {
+float time_layouts_in_graph(Ctx& c, const double* rhs, double* out, int vspmv, int vtrsv) {
+  if (!c.tune_forced.p) {
+    const int32_t h[2] = {kTuneInner, kTuneInner};
+    c.tune_forced.upload(h, 2, c.stream);
+  }
+  gb_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.tol = 0.0;
+  o.inner_tol = 1e-2;
+  o.precision = std::is_same<T, float>::value ? GB_PREC_MIXED : GB_PREC_FP64;
+  o.max_outer = 1;
+  o.max_inner = 1000;
+  o.use_graph = 1;
+  o.pressure_block = GB_PRESSURE_DIAG;
+  o.stop_rule = GB_STOP_RESIDUAL;
+  o.velocity_block = GB_VELOCITY_IC0_PCG;
+  Args a = make_args(c, &o, 1);
+  a.forced = c.tune_forced.p;
+  a.nforced = 2;
+  Run<1, T> run(c, a);
+  run.vspmv = vspmv;
+  run.vtrsv = vtrsv;
+  cudaGraphExec_t g = run.build_graph(rhs, out);
+  cudaEvent_t e0, e1;
+  GBS_CUDA(cudaEventCreate(&e0));
+  GBS_CUDA(cudaEventCreate(&e1));
+  GBS_CUDA(cudaGraphLaunch(g, c.stream));
+  GBS_CUDA(cudaEventRecord(e0, c.stream));
+  GBS_CUDA(cudaGraphLaunch(g, c.stream));
+  GBS_CUDA(cudaGraphLaunch(g, c.stream));
+  GBS_CUDA(cudaEventRecord(e1, c.stream));
+  GBS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(g);
+  return ms / 2;
+}
+
+// Layout tuning for single-RHS solves, once per precision, outside any
+// graph capture, at the first solve (with its right-hand side):
+// * the inner SpMV: CSR (8 lanes per row) and SELL-32 (thread per row; 2 or
+//   4 warps per slice), each timed alone;
+// * the IC(0) sweeps: every available form (CSR, SELL-32, three staged, two
+//   packed, two split packed, SELL-32 with W warps per slice in four forms,
+//   TMA-staged SELL-32), each timed inside the graph of a short replayed solve
+//   (time_layouts_in_graph) with the chosen SpMV, so that the sweep is judged
+//   with the L2 contents, launch overlap and fused CG work it has in a solve
+//   (timed alone, a sweep finds much of the factor in L2 and the forms that
+//   prefetch least look best).
+// A form replaces the best so far only when it is 3 % faster.  The choice
+// only changes the summation order inside a row (and, for the SELL-family
+// forms, computes rho = r^T z as ||L^{-1} r||^2).
+template <class T>
+void autotune_single(Ctx& c, const double* rhs, double* out) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   staged_prepare<T>(c);
   if (c.var_spmv[pi] >= 0 && c.var_trsv[pi] >= 0) return;
   Workspace& w = c.ws;
-  k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_p, c.n_u, T(1));
-  k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_r, c.n_u, T(1));
-  const double live[2] = {1.0, 1.0};
-  GBS_CUDA(cudaMemcpyAsync(w.S + S_CG_ACTIVE, &live[0], sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  GBS_CUDA(cudaMemcpyAsync(w.S + S_RHO, &live[1], sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  Args a = make_args(c, nullptr, 1);
-  cudaEvent_t e0, e1;
-  GBS_CUDA(cudaEventCreate(&e0));
-  GBS_CUDA(cudaEventCreate(&e1));
-  auto time_it = [&](int variant, int which) {
-    Run<1, T> run(c, a);
-    if (which == 0) run.vspmv = variant;
-    else run.vtrsv = variant;
-    const int reps = which == 0 ? 20 : 5;
-    if (which == 0) {
+  if (c.var_spmv[pi] < 0) {
+    k_fill_value<T><<<grid_cap(c.n_u), kBlock, 0, c.stream>>>((T*)w.cg_p, c.n_u, T(1));
+    const double live[2] = {1.0, 1.0};
+    GBS_CUDA(cudaMemcpyAsync(w.S + S_CG_ACTIVE, &live[0], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    GBS_CUDA(cudaMemcpyAsync(w.S + S_RHO, &live[1], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    Args a = make_args(c, nullptr, 1);
+    cudaEvent_t e0, e1;
+    GBS_CUDA(cudaEventCreate(&e0));
+    GBS_CUDA(cudaEventCreate(&e1));
+    auto time_spmv = [&](int variant) {
+      Run<1, T> run(c, a);
+      run.vspmv = variant;
+      const int reps = 20;
       run.spmv();
       GBS_CUDA(cudaEventRecord(e0, c.stream));
       for (int r = 0; r < reps; ++r) run.spmv();
@@ -748,42 +900,26 @@ void autotune_single(Ctx& c) {
       float ms = 0.f;
       GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       return ms;
-    }
-    // an IC(0) application, each after an untimed SpMV that streams A_h
-    // through L2 as in the solve (back-to-back sweeps would find the factor
-    // in L2 and favour the forms that prefetch least)
-    float total = 0.f;
-    for (int r = 0; r <= reps; ++r) {
-      run.spmv();
-      GBS_CUDA(cudaEventRecord(e0, c.stream));
-      run.trsv_fwd();
-      run.trsv_bwd();
-      GBS_CUDA(cudaEventRecord(e1, c.stream));
-      GBS_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      GBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (r > 0) total += ms;
-    }
-    return total;
-  };
-  if (c.var_spmv[pi] < 0) {
-    float best = time_it(0, 0);
+    };
+    float best = time_spmv(0);
     int choice = 0;
     for (int v = 1; v <= 3; ++v) {
-      const float t = time_it(v, 0);
+      const float t = time_spmv(v);
       if (t < 0.97f * best) {
         best = t;
         choice = v;
       }
     }
     c.var_spmv[pi] = choice;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   }
   if (c.var_trsv[pi] < 0) {
-    float best = time_it(0, 1);
+    float best = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], 0);
     int choice = 0;
-    for (int v = 1; v <= 9; ++v) {
+    for (int v = 1; v <= 13; ++v) {
       if (!trsv_available(c, v)) continue;
-      const float t = time_it(v, 1);
+      const float t = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], v);
       if (t < 0.97f * best) {
         best = t;
         choice = v;
@@ -791,8 +927,6 @@ void autotune_single(Ctx& c) {
     }
     c.var_trsv[pi] = choice;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   GBS_CUDA(cudaGetLastError());
 }
 
@@ -836,7 +970,7 @@ void autotune_batch(Ctx& c) {
 
 template <int K, class T>
 void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solve_opts& o) {
-  if (K == 1) autotune_single<T>(c);
+  if (K == 1) autotune_single<T>(c, rhs, out);
   if (K > 1) autotune_batch<K, T>(c);
   Args a = make_args(c, &o, k);
   Run<K, T> run(c, a);
@@ -865,8 +999,16 @@ void dispatch_solve(Ctx& c, const double* rhs, double* out, int k, const gb_solv
 int collect_info(Ctx& c, int k, gb_info* info) {
   Workspace& w = c.ws;
   const int K = w.K;
+  int timeout = 0;
   GBS_CUDA(cudaMemcpyAsync(w.S_host, w.S, sizeof(double) * S_NFIELDS * K, cudaMemcpyDeviceToHost, c.stream));
+  GBS_CUDA(cudaMemcpyAsync(&timeout, c.status_d.p + 2, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));
+  if (timeout) {  // a bounded wait of a sweep gave up: the solution is not valid
+    GBS_CUDA(cudaMemsetAsync(c.status_d.p + 2, 0, sizeof(int), c.stream));
+    for (int t = 0; t < k; ++t) info[t].status = GB_ERR_DEVICE_TIMEOUT;
+    GBS_CUDA(cudaStreamSynchronize(c.stream));
+    return GB_ERR_DEVICE_TIMEOUT;
+  }
   int worst = GB_OK;
   for (int t = 0; t < k; ++t) {
     auto f = [&](int field) { return w.S_host[field * K + t]; };
@@ -965,7 +1107,7 @@ void release_workspace(Ctx& c) {
   void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
                   w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
                   w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out, w.qcg_x, w.qcg_r, w.qcg_z,
-                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2], w.lz};
+                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2], w.lz, w.rho_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w.S_host) cudaFreeHost(w.S_host);

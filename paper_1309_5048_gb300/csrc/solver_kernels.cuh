@@ -29,7 +29,11 @@ namespace gbs {
 namespace {
 
 constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
-constexpr int kSellwPF = 12;  // slots per lane loaded before the wait by k_trsv_level_sellw
+constexpr int kSellwPF = 12;      // slots per lane loaded before the wait by k_trsv_level_sellw
+constexpr int kSellwLitePF = 4;   // the same, light forms (layouts 11-13)
+constexpr int kTmaCap = (kBlock / 32) * 32 * kTmaPF;      // slots of one TMA stage (8 slices x 32 rows x kTmaPF)
+constexpr long long kTmaWaitPolls = 1LL << 26;            // bound on the polls of one stage wait
+constexpr unsigned long long kTmaWaitNs = 2000000000ULL;  // and on its wall time (2 s)
 
 // Device view of a SELL-32 matrix copy (see Sell in gbs_internal.h).
 struct SellView {
@@ -95,6 +99,13 @@ struct Args {
   // gamma_j at lz[(K + t) * lz_cap + j - 1]
   double* lz;
   int lz_cap;
+  // device error word: set to 1 by a kernel whose bounded wait ran out
+  int* dev_status;
+  // CG step fused into the IC(0) sweeps (SELL-family layouts): 0 off, 1 in
+  // the CG loop (rho, beta = rho / rho_old, p = z + beta p), 2 at the start of
+  // a CG solve (rho, p = z); per-block partials of rho over a forward sweep
+  int cg_fuse;
+  double* rho_part;
 };
 
 // The two inner CG solves: SYS 0 on A_h (velocity block, Sec. 5.1 "PCG(A)"),
@@ -800,6 +811,48 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_batch(Args a, int r0, int
   if (live) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
 }
 
+// ---- CG step fused into the IC(0) sweeps -----------------------------------
+// With M = L L^T the CG quantity rho = r^T z = r^T L^{-T} L^{-1} r equals
+// ||y||^2 for y = L^{-1} r, the forward sweep's output, so the forward sweep
+// can reduce rho and the backward sweep, which writes z, can update the
+// search direction p = z + beta p in the same pass (beta = rho / rho_old is
+// known once the forward sweep has completed).  Each forward level writes one
+// partial of y_i^2 per block to rho_part[pbase + block]; the last block of
+// the last forward level (plast = number of partials of the sweep) sums all
+// partials in a fixed order and sets rho and beta as k_cg_rho does.  With
+// a.cg_fuse == 0 nothing is done.  Called by every thread of the block.
+__device__ __forceinline__ void cg_fused_fwd_epilogue(const Args& a, double yy, int pbase, int plast) {
+  if (a.cg_fuse == 0) return;  // uniform
+  double vals[1] = {yy};
+  block_partials<1, 1>(vals, a.rho_part + pbase);
+  if (plast > 0 && last_block(a.counter)) {
+    __shared__ double tot[1];
+    finalize_partials<1, 1>(a.rho_part, plast, tot);
+    if (threadIdx.x == 0) {
+      if (SF(a, S_CG_ACTIVE, 0, 1) != 0.0) {
+        if (a.cg_fuse == 2) {
+          SF(a, S_RHO, 0, 1) = tot[0];
+        } else {
+          SF(a, S_ALPHA, 0, 1) = tot[0] / SF(a, S_RHO, 0, 1);  // beta
+          SF(a, S_RHO, 0, 1) = tot[0];
+        }
+      }
+      *a.counter = 0;
+    }
+  }
+}
+
+// The backward sweep's store of z_i, and with the fused CG step the update of
+// p_i (p = z at the start of a CG solve, else z + beta p).
+template <class T>
+__device__ __forceinline__ void cg_fused_bwd_store(const Args& a, T* out, int row, T z, T beta) {
+  out[row] = z;
+  if (a.cg_fuse != 0) {
+    T* p = (T*)a.cg_p;
+    p[row] = a.cg_fuse == 2 ? z : z + beta * p[row];
+  }
+}
+
 // ---- SELL-32 variants (single right-hand side, one thread per row) --------
 // The 32 lanes of a warp read 32 consecutive slots, so every load of values
 // and column indices is coalesced and no cross-lane reduction is needed (on
@@ -895,7 +948,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_sellw(Args a) {
 // (same recurrences and the same programmatic-dependent-launch structure as
 // k_trsv_level).
 template <class T, bool FWD>
-__global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int s1) {
+__global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int s1, int pbase, int plast) {
   constexpr int PF = 8;  // entries per row fetched before the wait
   cudaTriggerProgrammaticLaunchCompletion();
   const SellView m = FWD ? a.sL : a.sU;
@@ -925,32 +978,51 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
     ii = inv[row];
   }
   cudaGridDependencySynchronize();
-  if (!act) return;
   const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the store only
-  T sum = 0;
+  double yy = 0.0;
+  if (act) {
+    T sum = 0;
 #pragma unroll
-  for (int k = 0; k < PF; ++k)
-    if (k < len) sum += v[k] * __ldcg(out + cc[k]);
-  for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
-  if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
+    for (int k = 0; k < PF; ++k)
+      if (k < len) sum += v[k] * __ldcg(out + cc[k]);
+    for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
+    const T y = (__ldcg(rhs + row) - sum) * ii;
+    if (live) {
+      if (FWD) {
+        out[row] = y;
+        yy = (double)y * (double)y;
+      } else {
+        cg_fused_bwd_store<T>(a, out, row, y, (T)SF(a, S_ALPHA, 0, 1));
+      }
+    }
+  }
+  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
 }
 
 // One level of a triangular solve on the SELL-32 copy with W warps per
 // 32-row slice (same recurrences as k_trsv_level).  Warp h of a slice owns the
-// stencil slots k = h, h + W, ... of its 32 rows; before the wait for the
-// previous level each lane loads the column indices and factor values of its
-// first PF slots (coalesced: a warp reads one slot of 32 neighbouring rows),
-// with the streaming cache hint so that the factor, read once per sweep, does
-// not push the solution vector out of L2.  After the wait every lane issues
-// the gathers of all its solution entries at once -- one L2 round trip per
-// level -- and sums value * entry in slot order; the W partial sums of a row
-// are then added in warp order in shared memory.  The host picks W per level
-// so that PF slots per lane cover the level's longest row (slots beyond PF, if
-// any, are read after the wait).  One thread per row and lane keeps the FP64
-// issue at one DFMA per entry plus W - 1 DADDs per row.
+// stencil slots k = h, h + W, ... of its 32 rows; each lane loads the column
+// indices and factor values of its first PF slots (coalesced: a warp reads
+// one slot of 32 neighbouring rows) with the streaming cache hint, so that the
+// factor, read once per sweep, does not push the solution vector out of L2.
+// After the wait for the previous level every lane issues the gathers of
+// those PF solution entries at once and sums value * entry in slot order (the
+// FMAs stop at the warp's longest lane); the slots beyond PF are read in a
+// loop.  The W partial sums of a row are added in warp order in shared
+// memory.  One thread per row and lane keeps the FP64 issue at one DFMA per
+// entry plus W - 1 DADDs per row.  Forms: PF = 12 with W chosen so that PF
+// slots cover the level's longest row (layout 9); the light form PF = 4
+// (layouts 11-13) loops like the SELL SpMV with few registers and many warps
+// per SM, W chosen for about 16 (11, 13) or 8 (12) slots per lane.  A block
+// takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ... of the
+// level: one each when the grid covers every group (9, 11, 12), several in
+// turn on a grid of the resident blocks (13), so that a level a little larger
+// than one wave runs without a ragged second wave.  The first group's slots
+// are loaded before the wait (the factor does not depend on earlier levels).
 template <class T, bool FWD, int W, int PF>
-__global__ void __launch_bounds__(kBlock, 4) k_trsv_level_sellw(Args a, int s0, int s1) {
-  constexpr int SPB = kBlock / (32 * W);  // slices per block
+__global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Args a, int s0, int s1, int pbase,
+                                                                              int plast) {
+  constexpr int SPB = kBlock / (32 * W);  // slices per group
   static_assert(SPB * 32 * W == kBlock, "block shape");
   __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
   cudaTriggerProgrammaticLaunchCompletion();
@@ -961,47 +1033,310 @@ __global__ void __launch_bounds__(kBlock, 4) k_trsv_level_sellw(Args a, int s0, 
   T* out = (T*)(FWD ? a.cg_y : a.cg_z);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h = warp % W, ls = warp / W;
-  const int s = s0 + blockIdx.x * SPB + ls;
+  const int ngroups = (s1 - s0 + SPB - 1) / SPB;
   int row = -1, n = 0, base = 0;
+  T ii = T(0);
   int cc[PF];
   T v[PF];
-  T ii = T(0);
-  if (s < s1) {
-    const int r = m.row0[s] + lane;
-    if (r < m.row0[s + 1]) {
-      row = r;
-      const int len = m.rowlen[r];
-      n = len > h ? (len - h + W - 1) / W : 0;  // slots h, h + W, ... below len
-      base = m.off[s] + 32 * h + lane;
-      if (h == 0) ii = inv[r];
-    }
-  }
+  // the lane's row and first PF slots in group g (constant arrays only)
+#define GBS_SELLW_LANE(g)                                                  \
+  do {                                                                     \
+    row = -1;                                                              \
+    n = 0;                                                                 \
+    base = 0;                                                              \
+    ii = T(0);                                                             \
+    const int s_ = s0 + (g) * SPB + ls;                                    \
+    if ((g) < ngroups && s_ < s1) {                                        \
+      const int r_ = m.row0[s_] + lane;                                    \
+      if (r_ < m.row0[s_ + 1]) {                                           \
+        row = r_;                                                          \
+        const int len_ = m.rowlen[r_];                                     \
+        n = len_ > h ? (len_ - h + W - 1) / W : 0;                         \
+        base = m.off[s_] + 32 * h + lane;                                  \
+        if (h == 0) ii = inv[r_];                                          \
+      }                                                                    \
+    }                                                                      \
+    _Pragma("unroll") for (int u = 0; u < PF; ++u) {                       \
+      cc[u] = u < n ? __ldcs(m.col + base + 32 * W * u) : 0;               \
+      v[u] = u < n ? __ldcs(val + base + 32 * W * u) : T(0);               \
+    }                                                                      \
+  } while (0)
+  int g = blockIdx.x;
+  GBS_SELLW_LANE(g);
+  cudaGridDependencySynchronize();
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the stores only
+  const T beta = (T)SF(a, S_ALPHA, 0, 1);             // fused CG step (backward sweep)
+  double yy = 0.0;                                     // fused CG step (forward sweep)
+  for (bool first = true; g < ngroups; g += gridDim.x, first = false) {  // uniform over the block
+    if (!first) GBS_SELLW_LANE(g);
+    // FMAs stop at the warp's longest lane (a uniform exit): a fully unrolled
+    // predicated loop would issue all PF DFMAs, and the FP64 pipe (2 lanes
+    // per clock and SM) is as scarce as HBM bandwidth here.  Lanes past their
+    // own length add v = 0 times x = 0.
+    const int nw = __reduce_max_sync(0xffffffffu, n);
+    T xg[PF];
 #pragma unroll
-  for (int u = 0; u < PF; ++u) {
-    cc[u] = u < n ? __ldcs(m.col + base + 32 * W * u) : 0;
-    v[u] = u < n ? __ldcs(val + base + 32 * W * u) : T(0);
+    for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
+    T sum = 0;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      if (u >= nw) break;
+      sum += v[u] * xg[u];
+    }
+    for (int u = PF; u < n; ++u)
+      sum += __ldcs(val + base + 32 * W * u) * __ldcg(out + __ldcs(m.col + base + 32 * W * u));
+    if (W > 1) {
+      if (h > 0) part[h - 1][ls][lane] = sum;
+      __syncthreads();
+      if (h == 0) {
+#pragma unroll
+        for (int u = 0; u < W - 1; ++u) sum += part[u][ls][lane];
+      }
+    }
+    if (h == 0 && row >= 0) {
+      const T y = (__ldcg(rhs + row) - sum) * ii;
+      if (live) {
+        if (FWD) {
+          out[row] = y;
+          yy += (double)y * (double)y;
+        } else {
+          cg_fused_bwd_store<T>(a, out, row, y, beta);
+        }
+      }
+    }
+    if (W > 1) __syncthreads();  // part[] is reused by the next group
+  }
+#undef GBS_SELLW_LANE
+  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
+}
+
+// ---- TMA-staged SELL-32 variant (single right-hand side) ------------------
+// One level of a triangular solve (same recurrences as k_trsv_level) on the
+// SELL-32 copy, with the factor streamed into shared memory by the Tensor
+// Memory Accelerator.  The level's slices are cut into groups of 8 / W
+// consecutive slices (W warps per 32-row slice, chosen by the host from the
+// level's longest row so that W * kTmaPF slots cover it); the slots of a
+// group are contiguous in the SELL copy, so one bulk copy (cp.async.bulk,
+// completion counted in bytes on an mbarrier) moves its values and one its
+// column indices.  Each block takes groups g = blockIdx.x, blockIdx.x +
+// gridDim.x, ... through two shared-memory stages: the copies of its first
+// two groups are issued before the wait for the previous level (the factor
+// does not depend on it), and the copy of group i + 2 is issued as soon as
+// group i has been consumed.  The gathers of group i + 1's solution entries
+// are issued before the FMAs of group i, so the HBM stream of the factor, the
+// L2 gathers and the FP64 work overlap.  Warp h of a slice sums the slots h,
+// h + W, ... of its rows; the W partial sums of a row are added in warp order
+// in shared memory.  Every wait on a stage is bounded: after kTmaWaitNs (2 s)
+// the kernel sets *a.dev_status, skips the stage, waits (bounded again) for
+// its own copies in flight and returns.
+// Dynamic shared memory: 2 stages of kTmaCap values (T) and column indices,
+// then two 8-byte mbarriers.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_arrive(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// true once the phase with the given parity has completed
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for a stage: gives up after kTmaWaitNs of wall time (or kTmaWaitPolls
+// polls, whichever comes first) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  for (long long i = 0; i < kTmaWaitPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && global_ns() - t0 > kTmaWaitNs) return false;
+  }
+  return false;
+}
+
+// bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <class T, bool FWD, int W>
+__global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s1, int pbase, int plast) {
+  constexpr int SPB = kBlock / (32 * W);  // slices per group
+  static_assert(SPB * 32 * W == kBlock, "block shape");
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
+  __shared__ int oversize;
+  T* sval = reinterpret_cast<T*>(tma_smem);                                        // [2][kTmaCap]
+  int32_t* scol = reinterpret_cast<int32_t*>(tma_smem + 2 * kTmaCap * sizeof(T));  // [2][kTmaCap]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tma_smem + 2 * kTmaCap * (sizeof(T) + 4));
+  cudaTriggerProgrammaticLaunchCompletion();
+  const SellView m = FWD ? a.sL : a.sU;
+  const T* __restrict__ val = pick<T>(m.val, m.val32);
+  const T* __restrict__ inv = pick<T>(a.L_inv, a.L_inv32);
+  const T* rhs = (const T*)(FWD ? a.cg_r : a.cg_y);
+  T* out = (T*)(FWD ? a.cg_y : a.cg_z);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = warp % W, ls = warp / W;
+  const int ngroups = (s1 - s0 + SPB - 1) / SPB;
+  // the copy of group g into stage st (thread 0 only); a group larger than a
+  // stage (the host never launches one) is not copied and fails the block
+  auto issue = [&](int g, int st) {
+    const int sa = s0 + g * SPB, sb = min(sa + SPB, s1);
+    const int first = m.off[sa], slots = m.off[sb] - first;
+    if (slots > kTmaCap) {
+      oversize = 1;
+      mbar_arrive(&bar[st]);
+    } else if (slots > 0) {
+      mbar_expect_arrive(&bar[st], (unsigned)(slots * (sizeof(T) + 4)));
+      bulk_g2s(sval + st * kTmaCap, val + first, (unsigned)(slots * sizeof(T)), &bar[st]);
+      bulk_g2s(scol + st * kTmaCap, m.col + first, (unsigned)(slots * 4), &bar[st]);
+    } else {
+      mbar_arrive(&bar[st]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    oversize = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < ngroups) issue(blockIdx.x, 0);
+    if ((int)blockIdx.x + (int)gridDim.x < ngroups) issue(blockIdx.x + gridDim.x, 1);
   }
   cudaGridDependencySynchronize();
-  T xg[PF];
+  const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the stores only
+  const T beta = (T)SF(a, S_ALPHA, 0, 1);             // fused CG step (backward sweep)
+  double yy = 0.0;                                     // fused CG step (forward sweep)
+  struct Lane {
+    int row, n, base;
+    T ii, rv;
+  };
+  auto lane_of = [&](int g) {
+    Lane L = {-1, 0, 0, T(0), T(0)};
+    const int sa = s0 + g * SPB, sb = min(sa + SPB, s1);
+    const int s = sa + ls;
+    if (s < sb) {
+      const int r = m.row0[s] + lane;
+      if (r < m.row0[s + 1]) {
+        L.row = r;
+        const int len = m.rowlen[r];
+        L.n = len > h ? (len - h + W - 1) / W : 0;
+        L.base = m.off[s] - m.off[sa] + 32 * h + lane;
+        if (h == 0) {
+          L.ii = inv[r];
+          L.rv = __ldcg(rhs + r);
+        }
+      }
+    }
+    return L;
+  };
+  bool failed = false;
+  // a stage is read only after its wait succeeded and its group was copied
+  // (an oversize group is not copied and leaves the stage's contents stale)
+  auto stage_ready = [&](int st, unsigned parity) {
+    const bool ok = mbar_wait_bounded(&bar[st], parity) && *(volatile int*)&oversize == 0;
+    if (!ok) failed = true;
+    return ok;
+  };
+  int it = 0;
+  T xa[kTmaPF], xb[kTmaPF];
+  Lane cur = {-1, 0, 0, T(0), T(0)};
+  int g = blockIdx.x;
+  if (g < ngroups) {
+    cur = lane_of(g);
+    if (!stage_ready(0, 0u)) cur.n = 0;
+    const int32_t* sc = scol;
 #pragma unroll
-  for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
-  T sum = 0;
+    for (int u = 0; u < kTmaPF; ++u) xa[u] = u < cur.n ? __ldcg(out + sc[cur.base + 32 * W * u]) : T(0);
+  }
+  for (; g < ngroups; g += gridDim.x, ++it) {  // uniform over the block
+    if (__syncthreads_or(failed || oversize)) break;
+    const int st = it & 1;
+    // start the next group: its lane data, its stage, its gathers
+    const int gn = g + gridDim.x;
+    Lane nxt = {-1, 0, 0, T(0), T(0)};
+    if (gn < ngroups) {
+      nxt = lane_of(gn);
+      if (!stage_ready(st ^ 1, (unsigned)(((it + 1) >> 1) & 1))) nxt.n = 0;
+      const int32_t* sc = scol + (st ^ 1) * kTmaCap;
 #pragma unroll
-  for (int u = 0; u < PF; ++u)
-    if (u < n) sum += v[u] * xg[u];
-  for (int u = PF; u < n; ++u) sum += __ldcs(val + base + 32 * W * u) * __ldcg(out + __ldcs(m.col + base + 32 * W * u));
-  if (W > 1) {
-    if (h > 0) part[h - 1][ls][lane] = sum;
-    __syncthreads();
-    if (h == 0) {
+      for (int u = 0; u < kTmaPF; ++u) xb[u] = u < nxt.n ? __ldcg(out + sc[nxt.base + 32 * W * u]) : T(0);
+    }
+    // this group's sums (uniform exit at the warp's longest lane; shorter
+    // lanes add 0 * 0)
+    const T* sv = sval + st * kTmaCap;
+    const int32_t* sc = scol + st * kTmaCap;
+    const int nw = __reduce_max_sync(0xffffffffu, cur.n);
+    T sum = 0;
+#pragma unroll
+    for (int u = 0; u < kTmaPF; ++u) {
+      if (u >= nw) break;
+      sum += (u < cur.n ? sv[cur.base + 32 * W * u] : T(0)) * xa[u];
+    }
+    for (int u = kTmaPF; u < cur.n; ++u) sum += sv[cur.base + 32 * W * u] * __ldcg(out + sc[cur.base + 32 * W * u]);
+    if (W > 1 && h > 0) part[h - 1][ls][lane] = sum;
+    __syncthreads();  // stage st and part[] fully read / written
+    if (W > 1 && h == 0) {
 #pragma unroll
       for (int u = 0; u < W - 1; ++u) sum += part[u][ls][lane];
     }
+    if (h == 0 && cur.row >= 0 && live) {
+      const T y = (cur.rv - sum) * cur.ii;
+      if (FWD) {
+        out[cur.row] = y;
+        yy += (double)y * (double)y;
+      } else {
+        cg_fused_bwd_store<T>(a, out, cur.row, y, beta);
+      }
+    }
+    if (threadIdx.x == 0 && g + 2 * (int)gridDim.x < ngroups) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of stage st before its refill
+      issue(g + 2 * gridDim.x, st);
+    }
+    if (W > 1) __syncthreads();  // part[] is reused by the next group
+    cur = nxt;
+#pragma unroll
+    for (int u = 0; u < kTmaPF; ++u) xa[u] = xb[u];
   }
-  if (h == 0 && row >= 0) {
-    const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the store only
-    if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
+  if ((failed || oversize) && threadIdx.x == 0) {
+    atomicExch(a.dev_status, 1);
+    // let the copies this block issued land before it exits (bounded)
+    for (int k = 0; k < 2; ++k) {
+      const int g2 = (int)blockIdx.x + (it + k) * (int)gridDim.x;
+      if (g2 < ngroups) mbar_wait_bounded(&bar[(it + k) & 1], (unsigned)(((it + k) >> 1) & 1));
+    }
   }
+  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
 }
 
 // ---- staged variant (single right-hand side) ------------------------------

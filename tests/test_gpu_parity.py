@@ -328,7 +328,8 @@ def test_edge_cases(oracle_mod, gb):
 LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr"), ("csr", "staged4"),
                 ("sell", "staged12"), ("csr", "staged32"), ("csr", "packed12"), ("sell", "packed32"),
                 ("sell2w", "packed32"), ("sell4w", "csr"), ("csr", "split12"), ("sell2w", "split32"),
-                ("sell", "sellw"), ("sell2w", "sellw")]
+                ("sell", "sellw"), ("sell2w", "sellw"), ("sell", "sellwl"), ("csr", "sellwl8"),
+                ("sell2w", "sellwlr")]
 
 
 @pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
@@ -338,7 +339,9 @@ def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p)
     SELL-32 thread per row) and of the IC(0) sweeps (also the staged and
     packed forms, whose levels are split over many blocks at 2D 40^2, and the
     SELL form with several warps per slice, whose rows in 3D and at degree 4
-    are longer than its prefetch) reproduces the oracle (<= 1e-10)."""
+    are longer than its prefetch) reproduces the oracle (<= 1e-10).  The SELL
+    forms also carry the inner CG step (rho reduced as ||L^{-1} r||^2 in the
+    forward sweep, the search direction updated in the backward sweep)."""
     ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
     assert ref.factor() < 0
     s.factor_ic0()
@@ -354,6 +357,40 @@ def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p)
     assert rel(x10.cpu().numpy(), xr10) <= 1e-7
 
 
+@pytest.mark.parametrize("N", [13, 60])
+def test_tma_sweep_replay_parity(oracle_mod, gb, N):
+    """The TMA-staged SELL sweep (factor slices streamed into shared memory by
+    bulk copies, two stages per block): at 2D 60^2 a level has about 340
+    slices, so blocks take several slice groups in turn through both stages
+    and the copies of later groups overlap the gathers of earlier ones."""
+    ref, s = make_pair(oracle_mod, gb, 2, N, 3, "multicolour")
+    assert ref.factor() < 0
+    s.factor_ic0()
+    for prec in ("fp64", "mixed"):
+        s.set_kernel_variants(prec, "sell", "tma")
+    assert s.kernel_variants("fp64") == ("sell", "tma")
+    b, rhs = _rhs(ref, s, "fourier", seed=12)
+    xr, ir = ref.minres(b, tol=1e-8, inner_tol=1e-2)
+    x, info = s.solve(rhs, tol=1e-8, inner_tol=1e-2, forced=ir["counts"])
+    assert info["status"] == 0
+    assert rel(x.cpu().numpy(), xr) <= 1e-10
+    x10, i10 = s.solve(rhs, tol=1e-10, inner_tol=1e-2, precision="mixed")
+    xr10, _ = ref.minres(b, tol=1e-10, inner_tol=1e-2)
+    assert i10["status"] == 0
+    assert rel(x10.cpu().numpy(), xr10) <= 1e-7
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 8, 4), (3, 3, 3)])
+def test_tma_sweep_is_refused_for_long_rows(gb, dim, N, p):
+    """Velocity degree 4 in 2D and every 3D problem have factor rows longer
+    than 88 entries, more than a slice group's stage holds: the layout is
+    refused with an invalid-argument status."""
+    s = gb.Stokes(dim, N, p, ordering="multicolour")
+    with pytest.raises(gb.GbError) as ei:
+        s.set_kernel_variants("fp64", "sell", "tma")
+    assert ei.value.status == 1
+
+
 def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     _, s = make_pair(oracle_mod, gb, 2, 20, 3, "multicolour")
     s.factor_ic0()
@@ -362,7 +399,8 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     s.solve(rhs, tol=1e-6)
     spmv, trsv = s.kernel_variants("fp64")
     assert spmv in ("csr", "sell", "sell2w", "sell4w") and trsv in ("csr", "sell", "staged4", "staged12", "staged32", "packed12",
-                                                 "packed32", "split12", "split32", "sellw")
+                                                 "packed32", "split12", "split32", "sellw", "tma", "sellwl",
+                                                 "sellwl8", "sellwlr")
 
 
 @pytest.mark.slow
