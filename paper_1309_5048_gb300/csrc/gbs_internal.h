@@ -146,7 +146,6 @@ struct Workspace {
   double* W[3] = {nullptr, nullptr, nullptr};
   double* q = nullptr;
   double* b = nullptr;  // right-hand side, internal layout
-  double* rho_part = nullptr;  // per-block partials of rho = ||L^{-1} r||^2 over a forward sweep
   double* R = nullptr;  // residual b - K x_j (2-norm stopping rule)
   double* lz = nullptr;  // Lanczos tridiagonal record [2][K][lz_cap]
   int lz_cap = 0;

@@ -68,9 +68,6 @@ void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
     w.flag = (int*)dmalloc(sizeof(int) * 8);
     GBS_CUDA(cudaMallocHost((void**)&w.flag_host, sizeof(int) * 8));
     w.partial = (double*)dmalloc(sizeof(double) * kRB * 32 * 4);
-    // one partial per block of a forward sweep of the SELL-family layouts
-    // (a level's grid never exceeds its slice count)
-    w.rho_part = (double*)dmalloc(sizeof(double) * ((size_t)c.sL.nslices + c.nlev + 1));
     w.counter = (unsigned*)dmalloc(64);
     w.aux = (double*)dmalloc(sizeof(double) * kRB * 32);
     GBS_CUDA(cudaMemsetAsync(w.counter, 0, 64, c.stream));
@@ -179,7 +176,6 @@ Args make_args(Ctx& c, const gb_solve_opts* o, int k) {
   a.lz = w.lz;
   a.lz_cap = w.lz_cap;
   a.dev_status = c.status_d.p + 2;
-  a.rho_part = w.rho_part;
   a.KW0 = w.KW[0];
   a.KW1 = w.KW[1];
   a.KW2 = w.KW[2];
@@ -368,7 +364,6 @@ struct Run {
   Args a;
   cudaStream_t s;
   int vspmv = 0, vtrsv = 0;  // single-RHS layouts (Ctx::var_spmv, Ctx::var_trsv)
-  int pbase = 0;             // partials of rho written so far in this forward sweep (fused CG step)
   int vbatch = 0;            // batched sweep (Ctx::var_trsv_batch)
   static constexpr int G = Map<K>::G;
   Run(Ctx& cc, Args aa) : c(cc), a(aa), s(cc.stream) {
@@ -414,11 +409,9 @@ struct Run {
     const int s0 = c.lev_slice[l], s1 = c.lev_slice[l + 1];
     constexpr int SPB = kBlock / (32 * W);
     int grid = std::max(1, (s1 - s0 + SPB - 1) / SPB);
-    if (resident) grid = std::min(grid, c.n_sm * 5);  // the resident blocks of 256 threads (launch bounds: 5 per SM)
+    if (resident) grid = std::min(grid, c.n_sm * 4);  // the resident blocks of 256 threads (launch bounds: 4 per SM)
     cfg.gridDim = dim3((unsigned)grid);
-    const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
-    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, PF>, a, s0, s1, pbase, pl));
-    if (FWD) pbase += grid;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, PF>, a, s0, s1));
   }
   // TMA-staged SELL sweep: W from the level's longest row, a grid of at
   // most the resident blocks, each taking groups of 8 / W slices in turn.
@@ -431,9 +424,7 @@ struct Run {
     const int grid = std::min(groups, c.n_sm * std::max(1, c.tma_bps[pi]));
     cfg.gridDim = dim3((unsigned)grid);
     cfg.dynamicSmemBytes = tma_bytes<T>();
-    const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
-    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_tma<T, FWD, W>, a, s0, s1, pbase, pl));
-    if (FWD) pbase += grid;
+    GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_tma<T, FWD, W>, a, s0, s1));
   }
   template <bool FWD>
   void level(int l) {
@@ -573,14 +564,8 @@ struct Run {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sell) {
-      const int grid = (int)cfg.gridDim.x;
-      const int pl = (FWD && l == c.nlev - 1) ? pbase + grid : 0;
-      GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sell<T, FWD>, a, r0, r1, pbase, pl));
-      if (FWD) pbase += grid;
-    } else {
-      GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
-    }
+    if (sell) GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sell<T, FWD>, a, r0, r1));
+    else GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level<K, T, FWD>, a, r0, r1));
   }
   void spmv() {
     if (K == 1 && vspmv == 2) k_cg_spmv_sellw<T, 2><<<grid_cap((int64_t)c.sA.nslices * 64), kBlock, 0, s>>>(a);
@@ -589,7 +574,6 @@ struct Run {
     else k_cg_spmv<K, T><<<grid_cap(c.n_u * G), kBlock, 0, s>>>(a);
   }
   void trsv_fwd() {
-    pbase = 0;
     for (int l = 0; l < c.nlev; ++l) level<true>(l);
   }
   void trsv_bwd() {
@@ -605,19 +589,7 @@ struct Run {
       trsv_bwd();
     }
   }
-  // The CG step rho = r^T z, beta, p = z + beta p runs inside the IC(0)
-  // sweeps of the SELL-family layouts (cg_fused_fwd_epilogue,
-  // cg_fused_bwd_store); the other layouts launch k_cg_rho and k_cg_pupdate.
-  bool fused_cg() const {
-    return K == 1 && a.velocity_block == GB_VELOCITY_IC0_PCG && (vtrsv == 1 || vtrsv >= 9);
-  }
   void cg_prologue() {
-    if (fused_cg()) {
-      a.cg_fuse = 2;
-      vel_precond();
-      a.cg_fuse = 0;
-      return;
-    }
     vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 1);
   }
@@ -626,12 +598,6 @@ struct Run {
     k_cg_axpy<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
   }
   void cg_tail() {
-    if (fused_cg()) {
-      a.cg_fuse = 1;
-      vel_precond();
-      a.cg_fuse = 0;
-      return;
-    }
     vel_precond();
     k_cg_rho<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a, 0);
     k_cg_pupdate<K, T><<<grid_cap(c.n_u * K), kBlock, 0, s>>>(a);
@@ -867,12 +833,11 @@ float time_layouts_in_graph(Ctx& c, const double* rhs, double* out, int vspmv, i
 //   packed, two split packed, SELL-32 with W warps per slice in four forms,
 //   TMA-staged SELL-32), each timed inside the graph of a short replayed solve
 //   (time_layouts_in_graph) with the chosen SpMV, so that the sweep is judged
-//   with the L2 contents, launch overlap and fused CG work it has in a solve
-//   (timed alone, a sweep finds much of the factor in L2 and the forms that
-//   prefetch least look best).
+//   with the L2 contents and launch overlap it has in a solve (timed alone, a
+//   sweep finds much of the factor in L2 and the forms that prefetch least
+//   look best).
 // A form replaces the best so far only when it is 3 % faster.  The choice
-// only changes the summation order inside a row (and, for the SELL-family
-// forms, computes rho = r^T z as ||L^{-1} r||^2).
+// only changes the summation order inside a row.
 template <class T>
 void autotune_single(Ctx& c, const double* rhs, double* out) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
@@ -1107,7 +1072,7 @@ void release_workspace(Ctx& c) {
   void* ptrs[] = {w.x, w.V[0], w.V[1], w.V[2], w.Z[0], w.Z[1], w.W[0], w.W[1], w.W[2], w.q, w.b,
                   w.cg_x, w.cg_r, w.cg_z, w.cg_y, w.cg_p, w.cg_q, w.S, w.flag, w.forced, w.partial,
                   w.counter, w.aux, w.rhs_tmp, w.host_in, w.host_out, w.qcg_x, w.qcg_r, w.qcg_z,
-                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2], w.lz, w.rho_part};
+                  w.qcg_p, w.qcg_q, w.forced_q, w.R, w.KW[0], w.KW[1], w.KW[2], w.lz};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w.S_host) cudaFreeHost(w.S_host);

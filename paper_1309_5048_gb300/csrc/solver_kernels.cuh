@@ -101,11 +101,6 @@ struct Args {
   int lz_cap;
   // device error word: set to 1 by a kernel whose bounded wait ran out
   int* dev_status;
-  // CG step fused into the IC(0) sweeps (SELL-family layouts): 0 off, 1 in
-  // the CG loop (rho, beta = rho / rho_old, p = z + beta p), 2 at the start of
-  // a CG solve (rho, p = z); per-block partials of rho over a forward sweep
-  int cg_fuse;
-  double* rho_part;
 };
 
 // The two inner CG solves: SYS 0 on A_h (velocity block, Sec. 5.1 "PCG(A)"),
@@ -811,48 +806,6 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_batch(Args a, int r0, int
   if (live) out[ridx] = (__ldcg(rhs + ridx) - s) * ii;
 }
 
-// ---- CG step fused into the IC(0) sweeps -----------------------------------
-// With M = L L^T the CG quantity rho = r^T z = r^T L^{-T} L^{-1} r equals
-// ||y||^2 for y = L^{-1} r, the forward sweep's output, so the forward sweep
-// can reduce rho and the backward sweep, which writes z, can update the
-// search direction p = z + beta p in the same pass (beta = rho / rho_old is
-// known once the forward sweep has completed).  Each forward level writes one
-// partial of y_i^2 per block to rho_part[pbase + block]; the last block of
-// the last forward level (plast = number of partials of the sweep) sums all
-// partials in a fixed order and sets rho and beta as k_cg_rho does.  With
-// a.cg_fuse == 0 nothing is done.  Called by every thread of the block.
-__device__ __forceinline__ void cg_fused_fwd_epilogue(const Args& a, double yy, int pbase, int plast) {
-  if (a.cg_fuse == 0) return;  // uniform
-  double vals[1] = {yy};
-  block_partials<1, 1>(vals, a.rho_part + pbase);
-  if (plast > 0 && last_block(a.counter)) {
-    __shared__ double tot[1];
-    finalize_partials<1, 1>(a.rho_part, plast, tot);
-    if (threadIdx.x == 0) {
-      if (SF(a, S_CG_ACTIVE, 0, 1) != 0.0) {
-        if (a.cg_fuse == 2) {
-          SF(a, S_RHO, 0, 1) = tot[0];
-        } else {
-          SF(a, S_ALPHA, 0, 1) = tot[0] / SF(a, S_RHO, 0, 1);  // beta
-          SF(a, S_RHO, 0, 1) = tot[0];
-        }
-      }
-      *a.counter = 0;
-    }
-  }
-}
-
-// The backward sweep's store of z_i, and with the fused CG step the update of
-// p_i (p = z at the start of a CG solve, else z + beta p).
-template <class T>
-__device__ __forceinline__ void cg_fused_bwd_store(const Args& a, T* out, int row, T z, T beta) {
-  out[row] = z;
-  if (a.cg_fuse != 0) {
-    T* p = (T*)a.cg_p;
-    p[row] = a.cg_fuse == 2 ? z : z + beta * p[row];
-  }
-}
-
 // ---- SELL-32 variants (single right-hand side, one thread per row) --------
 // The 32 lanes of a warp read 32 consecutive slots, so every load of values
 // and column indices is coalesced and no cross-lane reduction is needed (on
@@ -948,7 +901,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_sellw(Args a) {
 // (same recurrences and the same programmatic-dependent-launch structure as
 // k_trsv_level).
 template <class T, bool FWD>
-__global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int s1, int pbase, int plast) {
+__global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int s1) {
   constexpr int PF = 8;  // entries per row fetched before the wait
   cudaTriggerProgrammaticLaunchCompletion();
   const SellView m = FWD ? a.sL : a.sU;
@@ -978,50 +931,44 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
     ii = inv[row];
   }
   cudaGridDependencySynchronize();
+  if (!act) return;
   const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the store only
-  double yy = 0.0;
-  if (act) {
-    T sum = 0;
+  T sum = 0;
 #pragma unroll
-    for (int k = 0; k < PF; ++k)
-      if (k < len) sum += v[k] * __ldcg(out + cc[k]);
-    for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
-    const T y = (__ldcg(rhs + row) - sum) * ii;
-    if (live) {
-      if (FWD) {
-        out[row] = y;
-        yy = (double)y * (double)y;
-      } else {
-        cg_fused_bwd_store<T>(a, out, row, y, (T)SF(a, S_ALPHA, 0, 1));
-      }
-    }
-  }
-  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
+  for (int k = 0; k < PF; ++k)
+    if (k < len) sum += v[k] * __ldcg(out + cc[k]);
+  for (int k = PF; k < len; ++k) sum += val[base + 32 * k] * __ldcg(out + m.col[base + 32 * k]);
+  if (live) out[row] = (__ldcg(rhs + row) - sum) * ii;
 }
 
 // One level of a triangular solve on the SELL-32 copy with W warps per
 // 32-row slice (same recurrences as k_trsv_level).  Warp h of a slice owns the
-// stencil slots k = h, h + W, ... of its 32 rows; each lane loads the column
-// indices and factor values of its first PF slots (coalesced: a warp reads
-// one slot of 32 neighbouring rows) with the streaming cache hint, so that the
-// factor, read once per sweep, does not push the solution vector out of L2.
-// After the wait for the previous level every lane issues the gathers of
-// those PF solution entries at once and sums value * entry in slot order (the
-// FMAs stop at the warp's longest lane); the slots beyond PF are read in a
-// loop.  The W partial sums of a row are added in warp order in shared
-// memory.  One thread per row and lane keeps the FP64 issue at one DFMA per
-// entry plus W - 1 DADDs per row.  Forms: PF = 12 with W chosen so that PF
-// slots cover the level's longest row (layout 9); the light form PF = 4
-// (layouts 11-13) loops like the SELL SpMV with few registers and many warps
-// per SM, W chosen for about 16 (11, 13) or 8 (12) slots per lane.  A block
-// takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ... of the
-// level: one each when the grid covers every group (9, 11, 12), several in
-// turn on a grid of the resident blocks (13), so that a level a little larger
-// than one wave runs without a ragged second wave.  The first group's slots
-// are loaded before the wait (the factor does not depend on earlier levels).
+// stencil slots k = h, h + W, ... of its 32 rows; a lane reads the column
+// indices and factor values of its slots coalesced (a warp reads one slot of
+// 32 neighbouring rows) with the streaming cache hint, so that the factor,
+// read once per sweep, does not push the solution vector out of L2, and sums
+// value * entry in slot order; the W partial sums of a row are added in warp
+// order in shared memory.  One thread per row and lane keeps the FP64 issue
+// at one DFMA per entry plus W - 1 DADDs per row, and the FMAs of a chunk stop
+// at the warp's longest lane (a predicated, fully unrolled loop would issue
+// every DFMA, and the FP64 pipe, 2 lanes per clock and SM, is as scarce as HBM
+// bandwidth here).  Two forms:
+// * PF = 12 (layout 9): a lane loads its first 12 slots before the wait for
+//   the previous level, gathers their solution entries at once after it, and
+//   reads any further slots in a loop; W is chosen so that 12 slots cover the
+//   level's longest row;
+// * PF = 4, the light form (layouts 11-13): the slots are taken in chunks of
+//   four, software-pipelined -- while the gathers of chunk c are in flight the
+//   column indices and values of chunk c + 1 are loaded -- so that a chunk
+//   costs the longer of the HBM and L2 round trips, not their sum; the first
+//   chunk is loaded before the wait; few registers and many warps per SM; W
+//   for about 16 (11, 13) or 8 (12) slots per lane.
+// A block takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
+// of the level: one each when the grid covers every group (9, 11, 12), or
+// several in turn on a grid of the resident blocks (13), so that a level a
+// little larger than one wave runs without a ragged second wave.
 template <class T, bool FWD, int W, int PF>
-__global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Args a, int s0, int s1, int pbase,
-                                                                              int plast) {
+__global__ void __launch_bounds__(kBlock, PF <= 4 ? 4 : 3) k_trsv_level_sellw(Args a, int s0, int s1) {
   constexpr int SPB = kBlock / (32 * W);  // slices per group
   static_assert(SPB * 32 * W == kBlock, "block shape");
   __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
@@ -1034,11 +981,12 @@ __global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Ar
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h = warp % W, ls = warp / W;
   const int ngroups = (s1 - s0 + SPB - 1) / SPB;
+  constexpr int SW = 32 * W;  // stride of a lane's consecutive slots
   int row = -1, n = 0, base = 0;
   T ii = T(0);
   int cc[PF];
   T v[PF];
-  // the lane's row and first PF slots in group g (constant arrays only)
+  // the lane's row and its first PF slots in group g (constant arrays only)
 #define GBS_SELLW_LANE(g)                                                  \
   do {                                                                     \
     row = -1;                                                              \
@@ -1057,34 +1005,53 @@ __global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Ar
       }                                                                    \
     }                                                                      \
     _Pragma("unroll") for (int u = 0; u < PF; ++u) {                       \
-      cc[u] = u < n ? __ldcs(m.col + base + 32 * W * u) : 0;               \
-      v[u] = u < n ? __ldcs(val + base + 32 * W * u) : T(0);               \
+      cc[u] = u < n ? __ldcs(m.col + base + SW * u) : 0;                   \
+      v[u] = u < n ? __ldcs(val + base + SW * u) : T(0);                   \
     }                                                                      \
   } while (0)
   int g = blockIdx.x;
   GBS_SELLW_LANE(g);
   cudaGridDependencySynchronize();
   const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the stores only
-  const T beta = (T)SF(a, S_ALPHA, 0, 1);             // fused CG step (backward sweep)
-  double yy = 0.0;                                     // fused CG step (forward sweep)
   for (bool first = true; g < ngroups; g += gridDim.x, first = false) {  // uniform over the block
     if (!first) GBS_SELLW_LANE(g);
-    // FMAs stop at the warp's longest lane (a uniform exit): a fully unrolled
-    // predicated loop would issue all PF DFMAs, and the FP64 pipe (2 lanes
-    // per clock and SM) is as scarce as HBM bandwidth here.  Lanes past their
-    // own length add v = 0 times x = 0.
-    const int nw = __reduce_max_sync(0xffffffffu, n);
-    T xg[PF];
-#pragma unroll
-    for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
+    const int nw = __reduce_max_sync(0xffffffffu, n);  // the warp's longest lane
     T sum = 0;
+    if (PF > 4) {
+      T xg[PF];
 #pragma unroll
-    for (int u = 0; u < PF; ++u) {
-      if (u >= nw) break;
-      sum += v[u] * xg[u];
+      for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        if (u >= nw) break;
+        sum += v[u] * xg[u];
+      }
+      for (int u = PF; u < n; ++u) sum += __ldcs(val + base + SW * u) * __ldcg(out + __ldcs(m.col + base + SW * u));
+    } else {
+      for (int c0 = 0; c0 < nw; c0 += PF) {  // uniform over the warp
+        T xg[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) xg[u] = c0 + u < n ? __ldcg(out + cc[u]) : T(0);
+        int cn[PF];
+        T vn[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          const int k = c0 + PF + u;
+          cn[u] = k < n ? __ldcs(m.col + base + SW * k) : 0;
+          vn[u] = k < n ? __ldcs(val + base + SW * k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          if (c0 + u >= nw) break;
+          sum += v[u] * xg[u];
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          cc[u] = cn[u];
+          v[u] = vn[u];
+        }
+      }
     }
-    for (int u = PF; u < n; ++u)
-      sum += __ldcs(val + base + 32 * W * u) * __ldcg(out + __ldcs(m.col + base + 32 * W * u));
     if (W > 1) {
       if (h > 0) part[h - 1][ls][lane] = sum;
       __syncthreads();
@@ -1093,21 +1060,10 @@ __global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Ar
         for (int u = 0; u < W - 1; ++u) sum += part[u][ls][lane];
       }
     }
-    if (h == 0 && row >= 0) {
-      const T y = (__ldcg(rhs + row) - sum) * ii;
-      if (live) {
-        if (FWD) {
-          out[row] = y;
-          yy += (double)y * (double)y;
-        } else {
-          cg_fused_bwd_store<T>(a, out, row, y, beta);
-        }
-      }
-    }
+    if (h == 0 && row >= 0 && live) out[row] = (__ldcg(rhs + row) - sum) * ii;
     if (W > 1) __syncthreads();  // part[] is reused by the next group
   }
 #undef GBS_SELLW_LANE
-  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
 }
 
 // ---- TMA-staged SELL-32 variant (single right-hand side) ------------------
@@ -1188,7 +1144,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 
 template <class T, bool FWD, int W>
-__global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s1, int pbase, int plast) {
+__global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s1) {
   constexpr int SPB = kBlock / (32 * W);  // slices per group
   static_assert(SPB * 32 * W == kBlock, "block shape");
   extern __shared__ __align__(128) unsigned char tma_smem[];
@@ -1235,8 +1191,6 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s
   }
   cudaGridDependencySynchronize();
   const bool live = SF(a, S_CG_ACTIVE, 0, 1) != 0.0;  // decides the stores only
-  const T beta = (T)SF(a, S_ALPHA, 0, 1);             // fused CG step (backward sweep)
-  double yy = 0.0;                                     // fused CG step (forward sweep)
   struct Lane {
     int row, n, base;
     T ii, rv;
@@ -1310,15 +1264,7 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s
 #pragma unroll
       for (int u = 0; u < W - 1; ++u) sum += part[u][ls][lane];
     }
-    if (h == 0 && cur.row >= 0 && live) {
-      const T y = (cur.rv - sum) * cur.ii;
-      if (FWD) {
-        out[cur.row] = y;
-        yy += (double)y * (double)y;
-      } else {
-        cg_fused_bwd_store<T>(a, out, cur.row, y, beta);
-      }
-    }
+    if (h == 0 && cur.row >= 0 && live) out[cur.row] = (cur.rv - sum) * cur.ii;
     if (threadIdx.x == 0 && g + 2 * (int)gridDim.x < ngroups) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of stage st before its refill
       issue(g + 2 * gridDim.x, st);
@@ -1336,7 +1282,6 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_tma(Args a, int s0, int s
       if (g2 < ngroups) mbar_wait_bounded(&bar[(it + k) & 1], (unsigned)(((it + k) >> 1) & 1));
     }
   }
-  if (FWD) cg_fused_fwd_epilogue(a, yy, pbase, plast);
 }
 
 // ---- staged variant (single right-hand side) ------------------------------

@@ -339,9 +339,7 @@ def test_single_rhs_layouts_replay_parity(oracle_mod, gb, spmv, trsv, dim, N, p)
     SELL-32 thread per row) and of the IC(0) sweeps (also the staged and
     packed forms, whose levels are split over many blocks at 2D 40^2, and the
     SELL form with several warps per slice, whose rows in 3D and at degree 4
-    are longer than its prefetch) reproduces the oracle (<= 1e-10).  The SELL
-    forms also carry the inner CG step (rho reduced as ||L^{-1} r||^2 in the
-    forward sweep, the search direction updated in the backward sweep)."""
+    are longer than its prefetch) reproduces the oracle (<= 1e-10)."""
     ref, s = make_pair(oracle_mod, gb, dim, N, p, "multicolour")
     assert ref.factor() < 0
     s.factor_ic0()
