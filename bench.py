@@ -42,6 +42,8 @@ WORKLOADS = {
     "2d16": dict(dim=2, N=16, p=3, desc="2D unit square, 16x16 elements, k'=2, nu=1, 16-mode Fourier forcing"),
     "3d32": dict(dim=3, N=32, p=3, desc="3D unit cube, 32^3 elements, k'=2, nu=1, 16-mode Fourier forcing"),
     "2d1024": dict(dim=2, N=1024, p=3, desc="2D unit square, 1024x1024 elements, k'=2, nu=1, Fourier forcing"),
+    # the same kernels on a quarter of the unknowns (profiling captures that must stay small)
+    "2d512": dict(dim=2, N=512, p=3, desc="2D unit square, 512x512 elements, k'=2, nu=1, Fourier forcing"),
     "3d48": dict(dim=3, N=48, p=3, desc="3D unit cube, 48^3 elements, k'=2, nu=1, Fourier forcing"),
     # the paper's own benchmark problem (Sec. 6.4); run it as in Table ic_pgc_tols_k2 with
     # --pressure pcg --tol 1e-12 --inner-tol 1e-3
@@ -217,6 +219,9 @@ def _definition(path, name):
 TRAFFIC_SOURCES = {
     ("ic0_apply", "packed"): [("solver_kernels.cuh", "k_trsv_level_packed"), ("setup.cpp", "build_packed")],
     ("ic0_apply", "split"): [("solver_kernels.cuh", "k_trsv_level_split"), ("setup.cpp", "build_packed")],
+    ("ic0_apply", "sellwl"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
+    ("ic0_apply", "sellwlr"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
+    ("ic0_apply", "sellw"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
 }
 
 

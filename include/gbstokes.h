@@ -289,10 +289,9 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * slice groups streamed into shared memory by bulk copies (cp.async.bulk with
  * an mbarrier), two stages per block, the first two groups fetched before the
  * wait (available when every factor row has at most 88 off-diagonal entries:
- * 2D with velocity degree 3), 11 the SELL form of 9 taking its slots in
- * chunks of four, the next chunk's factor entries loaded while the current
- * chunk's solution entries are gathered, the first chunk before the wait (W
- * for about 16 slots per lane), 12 the same with about 8 slots per lane,
+ * 2D with velocity degree 3), 11 the SELL form of 9 with four slots loaded
+ * before the wait and the rest read in a loop (W for about 16 slots per lane;
+ * few registers, many warps per SM), 12 the same with about 8 slots per lane,
  * 13 the form of 11 on a grid of the resident blocks, each taking several
  * slice groups of a level in turn.
  * -1 automatic.  Automatic (the default) times the layouts on this problem at

@@ -409,7 +409,7 @@ struct Run {
     const int s0 = c.lev_slice[l], s1 = c.lev_slice[l + 1];
     constexpr int SPB = kBlock / (32 * W);
     int grid = std::max(1, (s1 - s0 + SPB - 1) / SPB);
-    if (resident) grid = std::min(grid, c.n_sm * 4);  // the resident blocks of 256 threads (launch bounds: 4 per SM)
+    if (resident) grid = std::min(grid, c.n_sm * 5);  // the resident blocks of 256 threads (launch bounds: 5 per SM)
     cfg.gridDim = dim3((unsigned)grid);
     GBS_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_level_sellw<T, FWD, W, PF>, a, s0, s1));
   }

@@ -952,23 +952,21 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
 // at one DFMA per entry plus W - 1 DADDs per row, and the FMAs of a chunk stop
 // at the warp's longest lane (a predicated, fully unrolled loop would issue
 // every DFMA, and the FP64 pipe, 2 lanes per clock and SM, is as scarce as HBM
-// bandwidth here).  Two forms:
-// * PF = 12 (layout 9): a lane loads its first 12 slots before the wait for
-//   the previous level, gathers their solution entries at once after it, and
-//   reads any further slots in a loop; W is chosen so that 12 slots cover the
-//   level's longest row;
-// * PF = 4, the light form (layouts 11-13): the slots are taken in chunks of
-//   four, software-pipelined -- while the gathers of chunk c are in flight the
-//   column indices and values of chunk c + 1 are loaded -- so that a chunk
-//   costs the longer of the HBM and L2 round trips, not their sum; the first
-//   chunk is loaded before the wait; few registers and many warps per SM; W
-//   for about 16 (11, 13) or 8 (12) slots per lane.
+// bandwidth here).  A lane loads its first PF slots before the wait for the
+// previous level (the factor does not depend on it), gathers their solution
+// entries at once after it, and reads any further slots in a loop.  Two
+// forms: PF = 12 (layout 9), W chosen so that 12 slots cover the level's
+// longest row; the light form PF = 4 (layouts 11-13), which loops like the
+// SELL SpMV with few registers and many warps per SM, W for about 16 (11, 13)
+// or 8 (12) slots per lane.  (A software-pipelined light form -- the next
+// four slots loaded while the current four are gathered -- needed more
+// registers and was 15 % slower at 2D 1024^2.)
 // A block takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
 // of the level: one each when the grid covers every group (9, 11, 12), or
 // several in turn on a grid of the resident blocks (13), so that a level a
 // little larger than one wave runs without a ragged second wave.
 template <class T, bool FWD, int W, int PF>
-__global__ void __launch_bounds__(kBlock, PF <= 4 ? 4 : 3) k_trsv_level_sellw(Args a, int s0, int s1) {
+__global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Args a, int s0, int s1) {
   constexpr int SPB = kBlock / (32 * W);  // slices per group
   static_assert(SPB * 32 * W == kBlock, "block shape");
   __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
@@ -1016,42 +1014,16 @@ __global__ void __launch_bounds__(kBlock, PF <= 4 ? 4 : 3) k_trsv_level_sellw(Ar
   for (bool first = true; g < ngroups; g += gridDim.x, first = false) {  // uniform over the block
     if (!first) GBS_SELLW_LANE(g);
     const int nw = __reduce_max_sync(0xffffffffu, n);  // the warp's longest lane
+    T xg[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
     T sum = 0;
-    if (PF > 4) {
-      T xg[PF];
 #pragma unroll
-      for (int u = 0; u < PF; ++u) xg[u] = u < n ? __ldcg(out + cc[u]) : T(0);
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        if (u >= nw) break;
-        sum += v[u] * xg[u];
-      }
-      for (int u = PF; u < n; ++u) sum += __ldcs(val + base + SW * u) * __ldcg(out + __ldcs(m.col + base + SW * u));
-    } else {
-      for (int c0 = 0; c0 < nw; c0 += PF) {  // uniform over the warp
-        T xg[PF];
-#pragma unroll
-        for (int u = 0; u < PF; ++u) xg[u] = c0 + u < n ? __ldcg(out + cc[u]) : T(0);
-        int cn[PF];
-        T vn[PF];
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          const int k = c0 + PF + u;
-          cn[u] = k < n ? __ldcs(m.col + base + SW * k) : 0;
-          vn[u] = k < n ? __ldcs(val + base + SW * k) : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          if (c0 + u >= nw) break;
-          sum += v[u] * xg[u];
-        }
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          cc[u] = cn[u];
-          v[u] = vn[u];
-        }
-      }
+    for (int u = 0; u < PF; ++u) {
+      if (u >= nw) break;
+      sum += v[u] * xg[u];
     }
+    for (int u = PF; u < n; ++u) sum += __ldcs(val + base + SW * u) * __ldcg(out + __ldcs(m.col + base + SW * u));
     if (W > 1) {
       if (h > 0) part[h - 1][ls][lane] = sum;
       __syncthreads();
