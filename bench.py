@@ -255,7 +255,12 @@ def traffic_for(kernel, workload, trsv=None, precision=None):
     except (OSError, ValueError):
         return None
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("trsv") != trsv or e.get("precision") != precision:
+    if not e or e.get("precision") != precision:
+        return None
+    # a record may name several layouts that read the same data (e.g. the same
+    # kernel on two grid sizes)
+    names = e.get("trsv")
+    if trsv not in (names if isinstance(names, list) else [names]):
         return None
     h = source_hash(kernel, trsv)
     if h is None or e.get("src_hash") != h:

@@ -93,3 +93,16 @@ def test_traffic_lookup_matches_sources_layout_and_precision(tree):
     assert bench.traffic_for("ic0_apply", "2d256", "packed32", "fp64") is None
     (tree / "profiles" / "traffic.json").write_text("not json")
     assert bench.traffic_for("ic0_apply", "2d256", "packed32", "fp64") is None
+
+
+def test_a_record_may_name_several_layouts_of_one_kernel(tree):
+    """The light SELL-W sweep on a grid covering every slice group and on a
+    grid of the resident blocks reads the same data; one record serves both
+    names, and only those."""
+    h = bench.source_hash("ic0_apply", "sellwl")
+    assert h == bench.source_hash("ic0_apply", "sellwlr")
+    _record(tree, src_hash=h, trsv=["sellwl", "sellwlr"])
+    assert bench.traffic_for("ic0_apply", "2d256", "sellwl", "fp64") == 123456
+    assert bench.traffic_for("ic0_apply", "2d256", "sellwlr", "fp64") == 123456
+    assert bench.traffic_for("ic0_apply", "2d256", "sellwl8", "fp64") is None
+    assert bench.traffic_for("ic0_apply", "2d256", "packed32", "fp64") is None
