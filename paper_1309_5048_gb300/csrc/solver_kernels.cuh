@@ -957,12 +957,12 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
 // entries at once after it, and reads any further slots in a loop.  Two
 // forms: PF = 12 (layout 9), W chosen so that 12 slots cover the level's
 // longest row; the light form PF = 4 (layouts 11-13), which loops like the
-// SELL SpMV with few registers and many warps per SM, W for about 16 (11, 13)
-// or 8 (12) slots per lane.  (A software-pipelined light form -- the next
+// SELL SpMV with few registers and many warps per SM, W for about 16 (11, 13),
+// 8 (12) or 32 (14) slots per lane.  (A software-pipelined light form -- the next
 // four slots loaded while the current four are gathered -- needed more
 // registers and was 15 % slower at 2D 1024^2.)
 // A block takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
-// of the level: one each when the grid covers every group (9, 11, 12), or
+// of the level: one each when the grid covers every group (9, 11, 12, 14), or
 // several in turn on a grid of the resident blocks (13), so that a level a
 // little larger than one wave runs without a ragged second wave.
 template <class T, bool FWD, int W, int PF>
