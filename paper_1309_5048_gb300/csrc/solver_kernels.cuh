@@ -30,7 +30,8 @@ namespace {
 
 constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
 constexpr int kSellwPF = 12;      // slots per lane loaded before the wait by k_trsv_level_sellw
-constexpr int kSellwLitePF = 4;   // the same, light forms (layouts 11-13)
+constexpr int kSellwLitePF = 4;   // the same, light forms (layouts 11-14)
+constexpr int kSellwLite2PF = 2;  // the same, lightest form (layout 15)
 constexpr int kTmaCap = (kBlock / 32) * 32 * kTmaPF;      // slots of one TMA stage (8 slices x 32 rows x kTmaPF)
 constexpr long long kTmaWaitPolls = 1LL << 26;            // bound on the polls of one stage wait
 constexpr unsigned long long kTmaWaitNs = 2000000000ULL;  // and on its wall time (2 s)
@@ -958,7 +959,8 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
 // forms: PF = 12 (layout 9), W chosen so that 12 slots cover the level's
 // longest row; the light form PF = 4 (layouts 11-13), which loops like the
 // SELL SpMV with few registers and many warps per SM, W for about 16 (11, 13),
-// 8 (12) or 32 (14) slots per lane.  (A software-pipelined light form -- the next
+// 8 (12) or 32 (14) slots per lane; PF = 2 (layout 15), fewer registers still,
+// W for about 16 slots per lane.  (A software-pipelined light form -- the next
 // four slots loaded while the current four are gathered -- needed more
 // registers and was 15 % slower at 2D 1024^2.)
 // A block takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -966,7 +968,7 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
 // several in turn on a grid of the resident blocks (13), so that a level a
 // little larger than one wave runs without a ragged second wave.
 template <class T, bool FWD, int W, int PF>
-__global__ void __launch_bounds__(kBlock, PF <= 4 ? 5 : 3) k_trsv_level_sellw(Args a, int s0, int s1) {
+__global__ void __launch_bounds__(kBlock, PF <= 2 ? 6 : (PF <= 4 ? 5 : 3)) k_trsv_level_sellw(Args a, int s0, int s1) {
   constexpr int SPB = kBlock / (32 * W);  // slices per group
   static_assert(SPB * 32 * W == kBlock, "block shape");
   __shared__ T part[W > 1 ? W - 1 : 1][SPB][32];
