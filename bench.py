@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--spmv", choices=["auto", "csr", "sell", "sell2w", "sell4w"], default="auto",
                     help="single-RHS SpMV layout of the benchmark precision (auto: timed at the first solve)")
     ap.add_argument("--trsv", choices=["auto", "csr", "sell", "staged4", "staged12", "staged32", "packed12",
-                                       "packed32", "split12", "split32", "sellw", "tma", "sellwl", "sellwl8", "sellwlr", "sellwl32", "sellwl2"],
+                                       "packed32", "split12", "split32", "sellw", "tma", "sellwl", "sellwl8", "sellwlr", "sellwl32", "sellwl2",
+                                       "sellwl24", "sellwl48"],
                     default="auto",
                     help="single-RHS IC(0) sweep layout of the benchmark precision")
     ap.add_argument("--stop", choices=["residual", "estimate"], default="residual",

@@ -454,8 +454,9 @@ struct Run {
         else if (len <= 32) sellw_level<FWD, 2, kSellwLite2PF>(cfg, l);
         else if (len <= 64) sellw_level<FWD, 4, kSellwLite2PF>(cfg, l);
         else sellw_level<FWD, 8, kSellwLite2PF>(cfg, l);
-      } else {  // light form: about 16 (11, 13), 8 (12) or 32 (14) slots per lane; 13 on a resident grid
-        const int per = vtrsv == 12 ? 8 : (vtrsv == 14 ? 32 : 16);
+      } else {  // light form: about 16 (11, 13), 8 (12), 32 (14), 24 (16) or 48 (17) slots per lane;
+                // 13 on a resident grid
+        const int per = vtrsv == 12 ? 8 : vtrsv == 14 ? 32 : vtrsv == 16 ? 24 : vtrsv == 17 ? 48 : 16;
         const bool res = vtrsv == 13;
         if (len <= per) sellw_level<FWD, 1, kSellwLitePF>(cfg, l, res);
         else if (len <= 2 * per) sellw_level<FWD, 2, kSellwLitePF>(cfg, l, res);
@@ -835,7 +836,7 @@ float time_layouts_in_graph(Ctx& c, const double* rhs, double* out, int vspmv, i
 // * the inner SpMV: CSR (8 lanes per row) and SELL-32 (thread per row; 2 or
 //   4 warps per slice), each timed alone;
 // * the IC(0) sweeps: every available form (CSR, SELL-32, three staged, two
-//   packed, two split packed, SELL-32 with W warps per slice in six forms,
+//   packed, two split packed, SELL-32 with W warps per slice in eight forms,
 //   TMA-staged SELL-32), each timed inside the graph of a short replayed solve
 //   (time_layouts_in_graph) with the chosen SpMV, so that the sweep is judged
 //   with the L2 contents and launch overlap it has in a solve (timed alone, a
@@ -887,7 +888,7 @@ void autotune_single(Ctx& c, const double* rhs, double* out) {
   if (c.var_trsv[pi] < 0) {
     float best = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], 0);
     int choice = 0;
-    for (int v = 1; v <= 15; ++v) {
+    for (int v = 1; v <= 17; ++v) {
       if (!trsv_available(c, v)) continue;
       const float t = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], v);
       if (t < 0.97f * best) {
