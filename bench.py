@@ -65,7 +65,7 @@ def parse():
                     help="single-RHS SpMV layout of the benchmark precision (auto: timed at the first solve)")
     ap.add_argument("--trsv", choices=["auto", "csr", "sell", "staged4", "staged12", "staged32", "packed12",
                                        "packed32", "split12", "split32", "sellw", "tma", "sellwl", "sellwl8", "sellwlr", "sellwl32", "sellwl2",
-                                       "sellwl24", "sellwl48"],
+                                       "sellwl24", "sellwl48", "sellwlh"],
                     default="auto",
                     help="single-RHS IC(0) sweep layout of the benchmark precision")
     ap.add_argument("--stop", choices=["residual", "estimate"], default="residual",
@@ -223,6 +223,7 @@ TRAFFIC_SOURCES = {
     ("ic0_apply", "sellwl"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
     ("ic0_apply", "sellwlr"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
     ("ic0_apply", "sellw"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
+    ("ic0_apply", "sellwlh"): [("solver_kernels.cuh", "k_trsv_level_sellw"), ("layouts.cpp", "sell_layout")],
 }
 
 

@@ -295,7 +295,9 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * 13 the form of 11 on a grid of the resident blocks, each taking several
  * slice groups of a level in turn, 14 the form of 11 with about 32 slots per
  * lane, 15 the form of 11 with two slots loaded before the wait, 16 / 17 the
- * form of 11 with about 24 / 48 slots per lane.
+ * form of 11 with about 24 / 48 slots per lane, 18 the form of 14 whose
+ * levels of one warp per slice (rows of at most 32 entries) load 12 slots
+ * before the wait.
  * -1 automatic.  Automatic (the default) times the layouts on this problem at
  * the first single-RHS solve of that precision and keeps the fastest; the
  * layouts differ only in the summation order inside a row.  Values outside

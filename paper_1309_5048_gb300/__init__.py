@@ -274,7 +274,7 @@ class Stokes:
         return out
 
     LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "staged4": 2, "staged12": 3, "staged32": 4, "packed12": 5,
-               "packed32": 6, "split12": 7, "split32": 8, "sellw": 9, "tma": 10, "sellwl": 11, "sellwl8": 12, "sellwlr": 13, "sellwl32": 14, "sellwl2": 15, "sellwl24": 16, "sellwl48": 17}
+               "packed32": 6, "split12": 7, "split32": 8, "sellw": 9, "tma": 10, "sellwl": 11, "sellwl8": 12, "sellwlr": 13, "sellwl32": 14, "sellwl2": 15, "sellwl24": 16, "sellwl48": 17, "sellwlh": 18}
     SPMV_LAYOUTS = {"auto": -1, "csr": 0, "sell": 1, "sell2w": 2, "sell4w": 3}
 
     def set_kernel_variants(self, precision="fp64", spmv="auto", trsv="auto"):
@@ -294,8 +294,9 @@ class Stokes:
         a grid of the resident blocks, each taking several slice groups),
         'sellwl32' (the light form with about 32 slots per lane), 'sellwl2'
         (two slots loaded before the wait, about 16 per lane), 'sellwl24',
-        'sellwl48' (the light form with about 24 / 48 slots per lane), or
-        'auto'."""
+        'sellwl48' (the light form with about 24 / 48 slots per lane),
+        'sellwlh' (about 32 slots per lane, with 12 slots loaded before the
+        wait on the levels of one warp per slice), or 'auto'."""
         _check(load_library().gb_set_kernel_variants(self._h, PRECISIONS[precision], self.SPMV_LAYOUTS[spmv],
                                                       self.LAYOUTS[trsv]))
 

@@ -254,7 +254,7 @@ int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double*
 
 int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
   if (!h) return bad_arg("null context");
-  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 17) {
+  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 18) {
     set_error("bad kernel variant request");
     return GB_ERR_INVALID_ARG;
   }

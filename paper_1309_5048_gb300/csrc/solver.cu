@@ -449,6 +449,11 @@ struct Run {
         else if (len <= 2 * kTmaPF) tma_level<FWD, 2>(cfg, l);
         else if (len <= 4 * kTmaPF) tma_level<FWD, 4>(cfg, l);
         else tma_level<FWD, 8>(cfg, l);
+      } else if (vtrsv == 18) {  // about 32 slots per lane; levels of one warp per slice prefetch 12 slots
+        if (len <= 32) sellw_level<FWD, 1, kSellwPF>(cfg, l);
+        else if (len <= 64) sellw_level<FWD, 2, kSellwLitePF>(cfg, l);
+        else if (len <= 128) sellw_level<FWD, 4, kSellwLitePF>(cfg, l);
+        else sellw_level<FWD, 8, kSellwLitePF>(cfg, l);
       } else if (vtrsv == 15) {  // lightest form: two slots before the wait, about 16 per lane
         if (len <= 16) sellw_level<FWD, 1, kSellwLite2PF>(cfg, l);
         else if (len <= 32) sellw_level<FWD, 2, kSellwLite2PF>(cfg, l);
@@ -836,7 +841,7 @@ float time_layouts_in_graph(Ctx& c, const double* rhs, double* out, int vspmv, i
 // * the inner SpMV: CSR (8 lanes per row) and SELL-32 (thread per row; 2 or
 //   4 warps per slice), each timed alone;
 // * the IC(0) sweeps: every available form (CSR, SELL-32, three staged, two
-//   packed, two split packed, SELL-32 with W warps per slice in eight forms,
+//   packed, two split packed, SELL-32 with W warps per slice in nine forms,
 //   TMA-staged SELL-32), each timed inside the graph of a short replayed solve
 //   (time_layouts_in_graph) with the chosen SpMV, so that the sweep is judged
 //   with the L2 contents and launch overlap it has in a solve (timed alone, a
@@ -888,7 +893,7 @@ void autotune_single(Ctx& c, const double* rhs, double* out) {
   if (c.var_trsv[pi] < 0) {
     float best = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], 0);
     int choice = 0;
-    for (int v = 1; v <= 17; ++v) {
+    for (int v = 1; v <= 18; ++v) {
       if (!trsv_available(c, v)) continue;
       const float t = time_layouts_in_graph<T>(c, rhs, out, c.var_spmv[pi], v);
       if (t < 0.97f * best) {

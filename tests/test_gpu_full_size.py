@@ -186,7 +186,7 @@ def test_3d_degree_5_without_block_layouts(gb):
     rhs[: s.n_u] = s.load_fourier(kap, amp)
     x, info = s.solve(rhs, tol=1e-6, inner_tol=1e-2, max_outer=1500, pressure="pcg")
     assert s.kernel_variants("fp64")[1] in ("csr", "sell", "sellw", "sellwl", "sellwl8", "sellwlr", "sellwl32",
-                                            "sellwl2", "sellwl24", "sellwl48")
+                                            "sellwl2", "sellwl24", "sellwl48", "sellwlh")
     assert info["status"] == 0 and info["relres_true"] <= 1.01e-6
     r = rhs - s.apply("K", x)
     rel = float(r.norm() / rhs.norm())

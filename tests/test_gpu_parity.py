@@ -330,7 +330,7 @@ LAYOUT_PAIRS = [("csr", "csr"), ("sell", "sell"), ("csr", "sell"), ("sell", "csr
                 ("sell2w", "packed32"), ("sell4w", "csr"), ("csr", "split12"), ("sell2w", "split32"),
                 ("sell", "sellw"), ("sell2w", "sellw"), ("sell", "sellwl"), ("csr", "sellwl8"),
                 ("sell2w", "sellwlr"), ("sell", "sellwl32"), ("csr", "sellwl2"),
-                ("sell", "sellwl24"), ("sell", "sellwl48")]
+                ("sell", "sellwl24"), ("sell", "sellwl48"), ("sell", "sellwlh")]
 
 
 @pytest.mark.parametrize("spmv,trsv", LAYOUT_PAIRS)
@@ -400,7 +400,7 @@ def test_layout_autotune_makes_a_choice(oracle_mod, gb):
     assert spmv in ("csr", "sell", "sell2w", "sell4w") and trsv in ("csr", "sell", "staged4", "staged12", "staged32", "packed12",
                                                  "packed32", "split12", "split32", "sellw", "tma", "sellwl",
                                                  "sellwl8", "sellwlr", "sellwl32",
-                                                 "sellwl2", "sellwl24", "sellwl48")
+                                                 "sellwl2", "sellwl24", "sellwl48", "sellwlh")
 
 
 @pytest.mark.slow
