@@ -298,9 +298,12 @@ int gb_apply(gb_ctx* ctx, int which, const double* x_dev, double* y_dev);
  * form of 11 with about 24 / 48 slots per lane, 18 the form of 14 whose
  * levels of one warp per slice (rows of at most 32 entries) load 12 slots
  * before the wait.
- * -1 automatic.  Automatic (the default) times the layouts on this problem at
- * the first single-RHS solve of that precision and keeps the fastest; the
- * layouts differ only in the summation order inside a row.  Values outside
+ * -1 automatic.  Automatic (the default) chooses at the first single-RHS
+ * solve of that precision: it times the SpMV layouts alone, then each sweep
+ * layout inside the graph of a one-step solve of this problem with 12 inner
+ * iterations per preconditioner application, and keeps the fastest (a later
+ * candidate must be 3 % faster to replace an earlier one).  The layouts
+ * differ only in the summation order inside a row.  Values outside
  * these ranges return GB_ERR_INVALID_ARG, and so do trsv 10 when a factor row
  * has more than 88 off-diagonal entries and trsv 2 - 8 when a row of
  * the factor has more than 2048 off-diagonal entries (3D with velocity degree
