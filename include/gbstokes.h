@@ -146,8 +146,10 @@ typedef struct {
   double relres_true;  /* ||b - K x||_2 / ||b||_2 recomputed at exit */
   int64_t q_inner_its_total; /* pressure CG iterations (GB_PRESSURE_PCG) */
   int q_inner_its_max;       /* largest pressure CG count of one application */
-  int status;          /* GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_NONFINITE or
-                          GB_ERR_INVALID_ARG (inconsistent pressure rhs) */
+  int status;          /* GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_NONFINITE,
+                          GB_ERR_INVALID_ARG (inconsistent pressure rhs) or
+                          GB_ERR_DEVICE_TIMEOUT (every column; the other
+                          fields are then not filled) */
 } gb_info;
 
 /* ---------------------------------------------------------------- setup --

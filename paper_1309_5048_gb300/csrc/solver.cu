@@ -998,15 +998,14 @@ int collect_info(Ctx& c, int k, gb_info* info) {
     I.q_inner_its_total = (int64_t)f(S_Q_TOTAL);
     I.q_inner_its_max = (int)f(S_Q_MAX);
     int st = GB_OK;
-    if (f(S_STATUS) == 3.0) st = GB_ERR_DEVICE_TIMEOUT;
-    else if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
+    if (f(S_NONFINITE) != 0.0) st = GB_ERR_NONFINITE;
     else if (f(S_INCONSISTENT) != 0.0) st = GB_ERR_INVALID_ARG;
     else if (f(S_STATUS) != 0.0) st = GB_ERR_NOT_CONVERGED;
     I.status = st;
-    // severity: device timeout > nonfinite > invalid argument > not converged
+    // severity: nonfinite > invalid argument > not converged (a device
+    // timeout has returned above for every column)
     auto rank = [](int v) {
-      return v == GB_ERR_DEVICE_TIMEOUT ? 4 : v == GB_ERR_NONFINITE ? 3 : v == GB_ERR_INVALID_ARG ? 2
-                                                                     : v == GB_ERR_NOT_CONVERGED ? 1 : 0;
+      return v == GB_ERR_NONFINITE ? 3 : v == GB_ERR_INVALID_ARG ? 2 : v == GB_ERR_NOT_CONVERGED ? 1 : 0;
     };
     if (rank(st) > rank(worst)) worst = st;
   }
