@@ -49,7 +49,8 @@ template <class T>
 void DevBuf<T>::upload(const T* host, size_t count, cudaStream_t s) {
   alloc(count);
   if (count) cuda_check(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
-  // pageable source: the copy is complete when cudaMemcpyAsync returns
+  // pageable source: it has been staged, and may be released, when
+  // cudaMemcpyAsync returns
 }
 
 template <class T>
@@ -254,7 +255,7 @@ int gb_dnu(gb_ctx* h, const double* lam_dev, const double* x_dev, int k, double*
 
 int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
   if (!h) return bad_arg("null context");
-  if (!h || precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 18) {
+  if (precision < 0 || precision > 1 || spmv < -1 || spmv > 3 || trsv < -1 || trsv > 18) {
     set_error("bad kernel variant request");
     return GB_ERR_INVALID_ARG;
   }
@@ -270,7 +271,7 @@ int gb_set_kernel_variants(gb_ctx* h, int precision, int spmv, int trsv) {
 
 int gb_set_batch_sweep(gb_ctx* h, int precision, int width, int variant) {
   if (!h) return bad_arg("null context");
-  if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || variant < -1 || variant > 1) {
+  if (precision < 0 || precision > 1 || (width != 8 && width != 32) || variant < -1 || variant > 1) {
     set_error("bad batch sweep request");
     return GB_ERR_INVALID_ARG;
   }
@@ -281,7 +282,7 @@ int gb_set_batch_sweep(gb_ctx* h, int precision, int width, int variant) {
 
 int gb_get_batch_sweep(const gb_ctx* h, int precision, int width, int* variant) {
   if (!h) return bad_arg("null context");
-  if (!h || precision < 0 || precision > 1 || (width != 8 && width != 32) || !variant) {
+  if (precision < 0 || precision > 1 || (width != 8 && width != 32) || !variant) {
     set_error("bad batch sweep query");
     return GB_ERR_INVALID_ARG;
   }
@@ -291,7 +292,7 @@ int gb_get_batch_sweep(const gb_ctx* h, int precision, int width, int* variant) 
 
 int gb_get_kernel_variants(const gb_ctx* h, int precision, int* spmv, int* trsv) {
   if (!h) return bad_arg("null context");
-  if (!h || precision < 0 || precision > 1 || !spmv || !trsv) {
+  if (precision < 0 || precision > 1 || !spmv || !trsv) {
     set_error("bad kernel variant query");
     return GB_ERR_INVALID_ARG;
   }

@@ -70,17 +70,17 @@ enum ScalarField {
   S_NFIELDS
 };
 
-// SELL-32 copy of a CSR matrix (single right-hand-side kernels, one thread per
-// row): rows are cut into slices of 32 consecutive rows that never cross a
-// level of the IC(0) DAG; entry k of the row in lane i of slice s sits at
-// off[s] + 32 k + i.  rowlen[row] bounds each row (padding is never read);
-// src maps every slot to the position of its value in the CSR value array
-// (-1 for padding), so values are refilled after assembly / factorisation.
 // Slots per lane and slice group of the TMA-staged SELL sweep: a level whose
 // longest factor row exceeds 8 * kTmaPF has no group that fits a stage, so
 // that layout is available only when every row of L and U is that short.
 constexpr int kTmaPF = 11;
 
+// SELL-32 copy of a CSR matrix (single right-hand-side kernels): rows are cut
+// into slices of 32 consecutive rows that never cross a level of the IC(0)
+// DAG; entry k of the row in lane i of slice s sits at off[s] + 32 k + i.
+// rowlen[row] bounds each row (padding is never read); src maps every slot to
+// the position of its value in the CSR value array (-1 for padding), so
+// values are refilled after assembly / factorisation.
 struct Sell {
   DevBuf<int32_t> off, row0, rowlen, col, src;
   DevBuf<double> val;
@@ -245,8 +245,11 @@ struct Ctx {
   // solves: SpMV 0 CSR with 8 lanes per row, 1 SELL-32 one thread per row,
   // 2/3 SELL-32 with 2/4 warps per slice;
   // triangular sweeps 0 CSR, 1 SELL-32, 2/3/4 staged with about 4/12/32
-  // entries per lane, 5/6 packed with about 12/32 entries per lane; -1 not
-  // chosen yet (timed at the first single-RHS solve)
+  // entries per lane, 5/6 packed with about 12/32 entries per lane, 7/8 split
+  // packed, 9 and 11-18 SELL-32 with W warps per slice (9: 12 slots loaded
+  // before the dependency wait; 11-17 light forms; 18 the hybrid of 14 and
+  // 9), 10 TMA-staged SELL-32; -1 not chosen yet (chosen at the first
+  // single-RHS solve by autotune_single)
   int var_spmv[2] = {-1, -1}, var_trsv[2] = {-1, -1};
   // batched sweeps per precision and width (index 0: K = 8, 1: K = 32): 0 the
   // warp-per-row kernel, 1 the staged batched kernel, -1 not chosen yet

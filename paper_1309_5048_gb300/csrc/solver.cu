@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -33,57 +34,73 @@ void* dmalloc(size_t bytes) {
   return p;
 }
 
+// Allocates the solve workspace for batch width K and the precision's inner
+// CG element size (called on an empty workspace).
+void alloc_workspace(Ctx& c, int K, int precision, size_t n) {
+  Workspace& w = c.ws;
+  w.K = K;
+  w.precision = precision;
+  w.n = n;
+  const size_t esz = precision == GB_PREC_MIXED ? 4 : 8;
+  const size_t vb = n * K * sizeof(double), cb = (size_t)c.n_u * K * esz;
+  w.x = (double*)dmalloc(vb);
+  for (int i = 0; i < 3; ++i) w.V[i] = (double*)dmalloc(vb);
+  for (int i = 0; i < 2; ++i) w.Z[i] = (double*)dmalloc(vb);
+  for (int i = 0; i < 3; ++i) w.W[i] = (double*)dmalloc(vb);
+  w.q = (double*)dmalloc(vb);
+  w.b = (double*)dmalloc(vb);
+  w.R = (double*)dmalloc(vb);
+  for (int i = 0; i < 3; ++i) w.KW[i] = (double*)dmalloc(vb);
+  w.cg_x = dmalloc(cb);
+  w.cg_r = dmalloc(cb);
+  w.cg_z = dmalloc(cb);
+  w.cg_y = dmalloc(cb);
+  w.cg_p = dmalloc(cb);
+  w.cg_q = dmalloc(cb);
+  const size_t qb = (size_t)c.n_p * K * esz;
+  w.qcg_x = dmalloc(qb);
+  w.qcg_r = dmalloc(qb);
+  w.qcg_z = dmalloc(qb);
+  w.qcg_p = dmalloc(qb);
+  w.qcg_q = dmalloc(qb);
+  w.S = (double*)dmalloc(sizeof(double) * S_NFIELDS * K);
+  GBS_CUDA(cudaMallocHost((void**)&w.S_host, sizeof(double) * S_NFIELDS * K));
+  w.flag = (int*)dmalloc(sizeof(int) * 8);
+  GBS_CUDA(cudaMallocHost((void**)&w.flag_host, sizeof(int) * 8));
+  w.partial = (double*)dmalloc(sizeof(double) * kRB * 32 * 4);
+  w.counter = (unsigned*)dmalloc(64);
+  w.aux = (double*)dmalloc(sizeof(double) * kRB * 32);
+  GBS_CUDA(cudaMemsetAsync(w.counter, 0, 64, c.stream));
+  GBS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int) * 8, c.stream));
+  GBS_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * S_NFIELDS * K, c.stream));
+  w.graph_valid = false;
+}
+
 void ensure_workspace(Ctx& c, int K, int precision, int k_io) {
   Workspace& w = c.ws;
   const size_t n = (size_t)(c.n_u + c.n_p);
   if (!(w.K == K && w.precision == precision && w.n == n && w.x)) {
     release_workspace(c);
-    w.K = K;
-    w.precision = precision;
-    w.n = n;
-    const size_t esz = precision == GB_PREC_MIXED ? 4 : 8;
-    const size_t vb = n * K * sizeof(double), cb = (size_t)c.n_u * K * esz;
-    w.x = (double*)dmalloc(vb);
-    for (int i = 0; i < 3; ++i) w.V[i] = (double*)dmalloc(vb);
-    for (int i = 0; i < 2; ++i) w.Z[i] = (double*)dmalloc(vb);
-    for (int i = 0; i < 3; ++i) w.W[i] = (double*)dmalloc(vb);
-    w.q = (double*)dmalloc(vb);
-    w.b = (double*)dmalloc(vb);
-    w.R = (double*)dmalloc(vb);
-    for (int i = 0; i < 3; ++i) w.KW[i] = (double*)dmalloc(vb);
-    w.cg_x = dmalloc(cb);
-    w.cg_r = dmalloc(cb);
-    w.cg_z = dmalloc(cb);
-    w.cg_y = dmalloc(cb);
-    w.cg_p = dmalloc(cb);
-    w.cg_q = dmalloc(cb);
-    const size_t qb = (size_t)c.n_p * K * esz;
-    w.qcg_x = dmalloc(qb);
-    w.qcg_r = dmalloc(qb);
-    w.qcg_z = dmalloc(qb);
-    w.qcg_p = dmalloc(qb);
-    w.qcg_q = dmalloc(qb);
-    w.S = (double*)dmalloc(sizeof(double) * S_NFIELDS * K);
-    GBS_CUDA(cudaMallocHost((void**)&w.S_host, sizeof(double) * S_NFIELDS * K));
-    w.flag = (int*)dmalloc(sizeof(int) * 8);
-    GBS_CUDA(cudaMallocHost((void**)&w.flag_host, sizeof(int) * 8));
-    w.partial = (double*)dmalloc(sizeof(double) * kRB * 32 * 4);
-    w.counter = (unsigned*)dmalloc(64);
-    w.aux = (double*)dmalloc(sizeof(double) * kRB * 32);
-    GBS_CUDA(cudaMemsetAsync(w.counter, 0, 64, c.stream));
-    GBS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int) * 8, c.stream));
-    GBS_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * S_NFIELDS * K, c.stream));
-    w.graph_valid = false;
+    // an allocation that fails part way releases everything, so that a
+    // half-built workspace never passes the check above
+    try {
+      alloc_workspace(c, K, precision, n);
+    } catch (...) {
+      release_workspace(c);
+      throw;
+    }
   }
   if (k_io > 0 && w.k < k_io) {
-    if (w.rhs_tmp) cudaFree(w.rhs_tmp);
-    if (w.host_in) cudaFree(w.host_in);
-    if (w.host_out) cudaFree(w.host_out);
+    w.graph_valid = false;
+    for (double** b : {&w.rhs_tmp, &w.host_in, &w.host_out}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    w.k = 0;
     w.rhs_tmp = (double*)dmalloc(sizeof(double) * n * k_io);
     w.host_in = (double*)dmalloc(sizeof(double) * n * k_io);
     w.host_out = (double*)dmalloc(sizeof(double) * n * k_io);
     w.k = k_io;
-    w.graph_valid = false;
   }
 }
 
@@ -281,8 +298,6 @@ size_t staged_bytes(const Ctx& c) {
   return staged_smem_bytes(std::max(c.tL.ecap, c.tU.ecap), std::max(c.tL.rcap, c.tU.rcap), sizeof(T));
 }
 
-// Raise the dynamic shared-memory limit of the staged sweep kernels to what
-// the partitions of this problem need (outside any graph capture).
 // Shared memory and row capacity of k_trsv_level_batch.
 int batch_capr(const Ctx& c) { return std::max(1, std::min(c.max_lrow, 512)); }
 template <int K, class T>
@@ -329,6 +344,9 @@ void tma_prepare(Ctx& c) {
   c.tma_bps[pi] = std::max(1, bps);
 }
 
+// Raise the dynamic shared-memory limits of the sweep kernels that stage in
+// shared memory to what the layouts of this problem need (outside any graph
+// capture).
 template <class T>
 void staged_prepare(Ctx& c) {
   tma_prepare<T>(c);
@@ -1122,6 +1140,9 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
     const int cap = std::min(o.max_outer, 1 << 20) + 1;
     if (!w.lz || w.lz_cap < cap) {
       if (w.lz) cudaFree(w.lz);
+      w.lz = nullptr;
+      w.lz_cap = 0;
+      w.graph_valid = false;
       w.lz = (double*)dmalloc(sizeof(double) * 2 * (size_t)K * cap);
       w.lz_cap = cap;
       w.graph_valid = false;
@@ -1130,6 +1151,9 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
   if (o.forced_q_host) {
     if ((size_t)o.nforced_q > w.forced_q_cap) {
       if (w.forced_q) cudaFree(w.forced_q);
+      w.forced_q = nullptr;
+      w.forced_q_cap = 0;
+      w.graph_valid = false;
       w.forced_q = (int32_t*)dmalloc(sizeof(int32_t) * o.nforced_q);
       w.forced_q_cap = o.nforced_q;
       w.graph_valid = false;
@@ -1140,6 +1164,9 @@ int solve(Ctx& c, const double* rhs_dev, double* x_dev, int k, const gb_solve_op
   if (o.forced_inner_host) {
     if ((size_t)o.nforced > w.forced_cap) {
       if (w.forced) cudaFree(w.forced);
+      w.forced = nullptr;
+      w.forced_cap = 0;
+      w.graph_valid = false;
       w.forced = (int32_t*)dmalloc(sizeof(int32_t) * o.nforced);
       w.forced_cap = o.nforced;
       w.graph_valid = false;
@@ -1199,8 +1226,9 @@ int lanczos_coeffs(Ctx& c, int rhs, double* delta, double* gamma, int cap) {
   if (delta && n > 0)
     GBS_CUDA(cudaMemcpyAsync(delta, w.lz + (size_t)rhs * w.lz_cap, sizeof(double) * n, cudaMemcpyDeviceToHost,
                              c.stream));
-  if (gamma && cap > 0)
-    GBS_CUDA(cudaMemcpyAsync(gamma, w.lz + (size_t)(w.K + rhs) * w.lz_cap, sizeof(double) * std::min(j + 1, cap + 1),
+  const int ng = std::min(j + 1, cap + 1);
+  if (gamma && ng > 0)
+    GBS_CUDA(cudaMemcpyAsync(gamma, w.lz + (size_t)(w.K + rhs) * w.lz_cap, sizeof(double) * ng,
                              cudaMemcpyDeviceToHost, c.stream));
   GBS_CUDA(cudaStreamSynchronize(c.stream));
   return j;
