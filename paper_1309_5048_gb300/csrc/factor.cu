@@ -93,7 +93,7 @@ __global__ void k_sell_fill(int64_t slots, const int32_t* __restrict__ src, cons
 
 void sell_refill(Ctx& c, Sell& S, const double* csr_val) {
   if (S.slots == 0) return;
-  k_sell_fill<<<152 * 8, 256, 0, c.stream>>>(S.slots, S.src.p, csr_val, S.val.p, S.val32.p);
+  k_sell_fill<<<c.n_sm * 8, 256, 0, c.stream>>>(S.slots, S.src.p, csr_val, S.val.p, S.val32.p);
   GBS_CUDA(cudaGetLastError());
 }
 
@@ -148,7 +148,7 @@ int64_t factor_ic0(Ctx& c) {
   }
   GBS_CUDA(cudaGetLastError());
   const int nnzL = (int)(c.nnzL - c.n_u), nnzU = nnzL;
-  k_factor_finish<<<152 * 8, 256, 0, c.stream>>>(n, nnzL, nnzU, c.L_val.p, c.L_inv.p, c.U_map.p,
+  k_factor_finish<<<c.n_sm * 8, 256, 0, c.stream>>>(n, nnzL, nnzU, c.L_val.p, c.L_inv.p, c.U_map.p,
                                                  c.U_val.p, c.L_val32.p, c.U_val32.p, c.L_inv32.p);
   GBS_CUDA(cudaGetLastError());
   sell_refill(c, c.sL, c.L_val.p);
