@@ -29,8 +29,8 @@ namespace gbs {
 namespace {
 
 constexpr int kRB = 1216;  // max blocks of the reduction kernels: 152 SMs x 8 blocks of 256 threads
-constexpr int kSellwPF = 12;      // slots per lane loaded before the wait by k_trsv_level_sellw
-constexpr int kSellwLitePF = 4;   // the same, light forms (layouts 11-14, 16, 17)
+constexpr int kSellwPF = 12;      // slots per lane loaded before the wait by k_trsv_level_sellw (layout 9; 18 on one-warp levels)
+constexpr int kSellwLitePF = 4;   // the same, light forms (layouts 11-14, 16, 17; 18 on the other levels)
 constexpr int kSellwLite2PF = 2;  // the same, lightest form (layout 15)
 constexpr int kTmaCap = (kBlock / 32) * 32 * kTmaPF;      // slots of one TMA stage (8 slices x 32 rows x kTmaPF)
 constexpr long long kTmaWaitPolls = 1LL << 26;            // bound on the polls of one stage wait
@@ -955,14 +955,16 @@ __global__ void __launch_bounds__(kBlock) k_trsv_level_sell(Args a, int s0, int 
 // every DFMA, and the FP64 pipe, 2 lanes per clock and SM, is as scarce as HBM
 // bandwidth here).  A lane loads its first PF slots before the wait for the
 // previous level (the factor does not depend on it), gathers their solution
-// entries at once after it, and reads any further slots in a loop.  Two
-// forms: PF = 12 (layout 9), W chosen so that 12 slots cover the level's
-// longest row; the light form PF = 4 (layouts 11-14, 16, 17), which loops
-// like the SELL SpMV with few registers and many warps per SM, W for about 16
-// (11, 13), 8 (12), 32 (14), 24 (16) or 48 (17) slots per lane; PF = 2 (layout
-// 15), fewer registers still, W for about 16 slots per lane.  (A software-pipelined light form -- the next
-// four slots loaded while the current four are gathered -- needed more
-// registers and was 15 % slower at 2D 1024^2.)
+// entries at once after it, and reads any further slots in a loop.  Three
+// prefetch depths: PF = 12 (layout 9, W chosen so that 12 slots cover the
+// level's longest row); the light form PF = 4 (layouts 11-14, 16, 17), which
+// loops like the SELL SpMV with few registers and many warps per SM, W for
+// about 16 (11, 13), 8 (12), 32 (14), 24 (16) or 48 (17) slots per lane;
+// PF = 2 (layout 15), fewer registers still, W for about 16 slots per lane.
+// The hybrid layout 18 is 14 with PF = 12 on its one-warp levels (rows of at
+// most 32 entries).  (A software-pipelined light form -- the next four slots
+// loaded while the current four are gathered -- needed more registers and
+// was 15 % slower at 2D 1024^2.)
 // A block takes the slice groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
 // of the level: one each when the grid covers every group (all but 13), or
 // several in turn on a grid of the resident blocks (13), so that a level a
